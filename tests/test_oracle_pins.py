@@ -1,0 +1,527 @@
+"""Pins for the FP64 CPU oracle, checked against things other than the oracle.
+
+Each pin comes from a closed form, a textbook identity, an independent
+library routine, brute force on tiny inputs, or a constant the paper prints
+(``tests/golden/paper_constants.txt``).  These tests need no GPU.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from synth import Scene, pinhole_camera, tiny_scene, uniform_box_scene, orbit_camera, subset_scene
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def paper_constants():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, value, _cite = line.split(" ", 2)
+        out[name] = float(value)
+    return out
+
+
+def one_scene(means, log_scales, quats, logits, dc, extra_sh=None):
+    n = len(means)
+    sh = np.zeros((n, 16, 3), np.float32)
+    sh[:, 0, :] = np.asarray(dc, np.float32).reshape(n, 3)
+    if extra_sh is not None:
+        sh[:, 1:, :] = extra_sh
+    f = lambda a, s: np.ascontiguousarray(np.asarray(a, np.float32).reshape(s))
+    return Scene(f(means, (n, 3)), f(log_scales, (n, 3)), f(quats, (n, 4)), f(logits, (n,)), sh)
+
+
+C0 = 1.0 / (2.0 * math.sqrt(math.pi))  # Y_0^0, from the definition
+
+
+def f32(v):
+    """The value as the renderer receives it (camera records are float32)."""
+    return float(np.float32(v))
+
+
+def dc_for_rgb(v):
+    """SH DC coefficient whose colour (C0 c + 0.5) is ``v``."""
+    return (v - 0.5) / C0
+
+
+# --------------------------------------------------------------------------
+# Spherical harmonics
+# --------------------------------------------------------------------------
+
+def test_sh_orthonormal_by_quadrature(oracle):
+    """Gram matrix of the 16 basis functions under exact sphere quadrature
+    (Gauss-Legendre in cos(theta), trapezoid in phi) is the identity."""
+    xs, ws = np.polynomial.legendre.leggauss(12)
+    nphi = 32
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    lm = [(l, m) for l in range(4) for m in range(-l, l + 1)]
+    G = np.zeros((16, 16))
+    for ct, wt in zip(xs, ws):
+        st = math.sqrt(1 - ct * ct)
+        for ph in phis:
+            d = (st * math.cos(ph), st * math.sin(ph), ct)
+            y = np.array([oracle.sh_basis(l, m, *d) for l, m in lm])
+            G += wt * (2 * np.pi / nphi) * np.outer(y, y)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_addition_theorem(oracle):
+    """sum_m Y_lm(u) Y_lm(v) = (2l + 1) / (4 pi) P_l(u . v)."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        u, v = rng.normal(size=3), rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        v /= np.linalg.norm(v)
+        for l in range(4):
+            lhs = sum(oracle.sh_basis(l, m, *u) * oracle.sh_basis(l, m, *v) for m in range(-l, l + 1))
+            coef = np.zeros(l + 1)
+            coef[l] = 1
+            rhs = (2 * l + 1) / (4 * np.pi) * np.polynomial.legendre.legval(float(u @ v), coef)
+            assert abs(lhs - rhs) < 1e-13
+
+
+def test_sh_cartesian_forms_condon_shortley(oracle):
+    """Textbook Cartesian forms of a few real SH, with the Condon-Shortley
+    phase (the sign convention of the 3DGS colour model)."""
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        d = rng.normal(size=3)
+        x, y, z = d / np.linalg.norm(d)
+        pi = math.pi
+        cases = {
+            (1, -1): -math.sqrt(3 / (4 * pi)) * y,
+            (1, 0): math.sqrt(3 / (4 * pi)) * z,
+            (1, 1): -math.sqrt(3 / (4 * pi)) * x,
+            (2, -2): 0.5 * math.sqrt(15 / pi) * x * y,
+            (2, -1): -0.5 * math.sqrt(15 / pi) * y * z,
+            (2, 0): 0.25 * math.sqrt(5 / pi) * (3 * z * z - 1),
+            (2, 2): 0.25 * math.sqrt(15 / pi) * (x * x - y * y),
+            (3, -3): -0.25 * math.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y),
+            (3, -2): 0.5 * math.sqrt(105 / pi) * x * y * z,
+            (3, 0): 0.25 * math.sqrt(7 / pi) * z * (5 * z * z - 3),
+            (3, 3): -0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y),
+        }
+        for (l, m), want in cases.items():
+            assert abs(oracle.sh_basis(l, m, x, y, z) - want) < 1e-13, (l, m)
+
+
+def test_colour_dc_only_and_clamp(oracle):
+    """With only the DC band, rgb = C0 c + 0.5, clamped at 0."""
+    cam = pinhole_camera(33, 33)
+    dc = np.array([[0.7, -0.2, -3.0]])
+    sc = one_scene([[0, 0, 3]], [[-3, -3, -3]], [[1, 0, 0, 0]], [0.0], dc)
+    pre = oracle.preprocess(sc, cam)
+    want = np.maximum(C0 * dc.astype(np.float32).astype(np.float64) + 0.5, 0)
+    np.testing.assert_allclose(pre["rgb"][0], want[0], atol=1e-15)
+    assert pre["rgb"][0, 2] == 0.0
+
+
+def test_colour_view_dependence_degree1(oracle):
+    """Degree-1 coefficient on Y_1^0 (index 2) tints along +z: a Gaussian on
+    the optical axis in front of a camera at the origin sees dir = +z."""
+    cam = pinhole_camera(33, 33)
+    extra = np.zeros((1, 15, 3), np.float32)
+    extra[0, 1, :] = [0.3, 0.0, -0.1]                  # k = 2 -> (l, m) = (1, 0)
+    sc = one_scene([[0, 0, 3]], [[-3, -3, -3]], [[1, 0, 0, 0]], [0.0], [[0, 0, 0]], extra)
+    pre = oracle.preprocess(sc, cam)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    want = np.maximum(np.float32(0.3) * c1 + 0.5, 0), 0.5, np.float32(-0.1) * c1 + 0.5
+    np.testing.assert_allclose(pre["rgb"][0], want, atol=1e-12)
+
+
+def _sh_cartesian(x, y, z):
+    """All 16 real SH (l <= 3, m = -l..l, Condon-Shortley phase) in their
+    textbook Cartesian forms on the unit sphere."""
+    pi = math.pi
+    a1 = math.sqrt(3 / (4 * pi))
+    return np.array([
+        1 / (2 * math.sqrt(pi)),
+        -a1 * y, a1 * z, -a1 * x,
+        0.5 * math.sqrt(15 / pi) * x * y,
+        -0.5 * math.sqrt(15 / pi) * y * z,
+        0.25 * math.sqrt(5 / pi) * (3 * z * z - 1),
+        -0.5 * math.sqrt(15 / pi) * x * z,
+        0.25 * math.sqrt(15 / pi) * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y),
+        0.5 * math.sqrt(105 / pi) * x * y * z,
+        -0.25 * math.sqrt(21 / (2 * pi)) * y * (5 * z * z - 1),
+        0.25 * math.sqrt(7 / pi) * z * (5 * z * z - 3),
+        -0.25 * math.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1),
+        0.25 * math.sqrt(105 / pi) * z * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y),
+    ])
+
+
+def test_colour_full_sh_from_orbit(oracle):
+    """Colour of every band, seen from cameras away from the origin: the
+    viewing direction runs from the camera centre (taken from the orbit's
+    own definition) to the mean, and rgb = max(0, sum_k c_k Y_k(dir) + 0.5)."""
+    rng = np.random.default_rng(21)
+    for k in (1, 7, 13):
+        cam = orbit_camera(k, 20, 4.0, 200, 150)
+        phi = 2 * math.pi * k / 20
+        campos = np.array([4.0 * math.sin(phi), 0.0, -4.0 * math.cos(phi)])
+        n = 40
+        means = rng.normal(scale=0.4, size=(n, 3))
+        sc = one_scene(means, [[-3.0] * 3] * n, [[1, 0, 0, 0]] * n, [0.0] * n, rng.normal(0, 0.5, (n, 3)),
+                       rng.normal(0, 0.3, (n, 15, 3)))
+        pre = oracle.preprocess(sc, cam)
+        vis = np.nonzero(pre["tiles"])[0]
+        assert len(vis) > 20
+        for g in vis:
+            d = sc.means[g].astype(np.float64) - campos
+            d /= np.linalg.norm(d)
+            want = np.maximum(_sh_cartesian(*d) @ sc.sh[g].astype(np.float64) + 0.5, 0.0)
+            np.testing.assert_allclose(pre["rgb"][g], want, atol=2e-6)  # campos from float32 viewmat
+
+
+# --------------------------------------------------------------------------
+# Projection (EWA) closed forms
+# --------------------------------------------------------------------------
+
+def test_single_isotropic_gaussian_closed_form(oracle):
+    """Isotropic Gaussian of scale s on the optical axis at depth z:
+    Sigma' = ((fx s / z)^2 + 0.3) I, mean at the principal point, radius
+    ceil(3 sqrt(sigma'^2 + sqrt(0.1))) (eigenvalue floor), and each pixel at
+    offset d gets alpha = min(0.99, o exp(-|d|^2 / (2 sigma'^2)))."""
+    cam = pinhole_camera(33, 33)  # odd size: principal point on pixel (16, 16)
+    log_s, z, logit, v = -4.0, 3.0, 0.4, 0.8
+    sc = one_scene([[0, 0, z]], [[log_s] * 3], [[1, 0, 0, 0]], [logit], [[dc_for_rgb(v)] * 3])
+    pre, srt, img = oracle.frame(sc, cam)
+    s = math.exp(float(np.float32(log_s)))
+    var = (f32(cam.fx) * s / z) ** 2 + 0.3
+    np.testing.assert_allclose(pre["xy"][0], [16.0, 16.0], atol=1e-12)
+    np.testing.assert_allclose(pre["cov2d"][0], [var, 0.0, var], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(pre["conic"][0], [1 / var, 0.0, 1 / var], rtol=1e-12, atol=1e-15)
+    assert pre["radius"][0] == math.ceil(3 * math.sqrt(var + math.sqrt(0.1)))
+    o = 1 / (1 + math.exp(-float(np.float32(logit))))
+    rgb = C0 * float(np.float32(dc_for_rgb(v))) + 0.5
+    for py in range(33):
+        for px in range(33):
+            d2 = (px - 16) ** 2 + (py - 16) ** 2
+            a = min(0.99, o * math.exp(-d2 / (2 * var)))
+            inside = (px // 16, py // 16)
+            r0 = pre["rect"][0]
+            covered = r0[0] <= inside[0] < r0[2] and r0[1] <= inside[1] < r0[3]
+            if a < 1 / 255 or not covered:
+                a = 0.0
+            assert abs(img["color"][0, py, px] - a * rgb) < 1e-12
+            assert abs(img["final_T"][py, px] - (1 - a)) < 1e-12
+            assert img["n_contrib"][py, px] == (1 if a > 0 else 0)
+
+
+def _quat_to_matrix_scipy(q):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q
+    return Rotation.from_quat([x, y, z, w]).as_matrix()
+
+
+def _projection(t, cam):
+    return np.array([f32(cam.fx) * t[0] / t[2] + f32(cam.cx), f32(cam.fy) * t[1] / t[2] + f32(cam.cy)])
+
+
+def test_anisotropic_rotated_ewa(oracle):
+    """Sigma' = J W Sigma W^T J^T + 0.3 I with Sigma from an independent
+    quaternion-to-matrix routine (scipy) and J the numerically
+    differentiated pinhole projection, for off-axis Gaussians seen by a
+    rotated camera."""
+    rng = np.random.default_rng(11)
+    cam = orbit_camera(3, 20, 4.0, 320, 240)
+    V = cam.viewmat.astype(np.float64)
+    for _ in range(20):
+        m = rng.normal(scale=0.5, size=3)
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        ls = rng.uniform(-4, -1, size=3)
+        sc = one_scene([m], [ls], [q], [0.0], [[0, 0, 0]])
+        pre = oracle.preprocess(sc, cam)
+        mf = sc.means[0].astype(np.float64)
+        Rm = _quat_to_matrix_scipy(sc.quats[0].astype(np.float64))
+        Sig = Rm @ np.diag(np.exp(2 * sc.log_scales[0].astype(np.float64))) @ Rm.T
+        t = V[:3, :3] @ mf + V[:3, 3]
+        assert abs(t[0] / t[2]) < 1.3 * cam.tan_fovx and abs(t[1] / t[2]) < 1.3 * cam.tan_fovy
+        J = np.zeros((2, 3))
+        for k in range(3):
+            h = 1e-6 * max(1.0, abs(t[k]))
+            e = np.zeros(3)
+            e[k] = h
+            J[:, k] = (_projection(t + e, cam) - _projection(t - e, cam)) / (2 * h)
+        W = V[:3, :3]
+        C = J @ W @ Sig @ W.T @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pre["cov2d"][0], [C[0, 0], C[0, 1], C[1, 1]], rtol=1e-6)
+        np.testing.assert_allclose(pre["xy"][0], _projection(t, cam), rtol=1e-12)
+        conic = np.linalg.inv(C)
+        np.testing.assert_allclose(pre["conic"][0], [conic[0, 0], conic[0, 1], conic[1, 1]], rtol=1e-6)
+
+
+def test_anisotropic_splat_pixels(oracle):
+    """Per-pixel alpha of one rotated, anisotropic splat: with Sigma' from the
+    preprocess (pinned above), alpha = min(0.99, o exp(-d^T Sigma'^-1 d / 2))
+    using an independent matrix inverse."""
+    cam = pinhole_camera(64, 48)
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    q /= np.linalg.norm(q)
+    sc = one_scene([[0.05, -0.03, 2.0]], [[-2.2, -3.6, -3.0]], [q], [1.2], [[dc_for_rgb(0.7)] * 3])
+    pre, srt, img = oracle.frame(sc, cam)
+    s00, s01, s11 = pre["cov2d"][0]
+    assert abs(s01) > 0.2 * math.sqrt(s00 * s11)  # genuinely rotated
+    Q = np.linalg.inv(np.array([[s00, s01], [s01, s11]]))
+    o = 1 / (1 + math.exp(-float(np.float32(1.2))))
+    rgb = pre["rgb"][0, 0]
+    x0, y0, x1, y1 = pre["rect"][0]
+    for py in range(cam.height):
+        for px in range(cam.width):
+            d = pre["xy"][0] - (px, py)
+            a = min(0.99, o * math.exp(-0.5 * d @ Q @ d))
+            if a < 1 / 255 or not (x0 <= px // 16 < x1 and y0 <= py // 16 < y1):
+                a = 0.0
+            assert abs(img["color"][0, py, px] - a * rgb) < 1e-12
+
+
+def test_frustum_clamped_jacobian(oracle):
+    """Outside 1.3 tan(fov) the Jacobian is taken at the clamped direction
+    (same depth), while the mean keeps its true projection."""
+    cam = pinhole_camera(64, 64)
+    z = 2.0
+    x = 3.0 * cam.tan_fovx * z  # far outside the clamp
+    sc = one_scene([[x, 0.0, z]], [[-1.5] * 3], [[1, 0, 0, 0]], [0.0], [[0, 0, 0]])
+    pre = oracle.preprocess(sc, cam)
+    s2 = math.exp(2 * float(np.float32(-1.5)))
+    fx, fy = f32(cam.fx), f32(cam.fy)
+    xc = 1.3 * f32(cam.tan_fovx) * z
+    J = np.array([[fx / z, 0, -fx * xc / z**2], [0, fy / z, 0]])
+    C = J @ (s2 * np.eye(3)) @ J.T + 0.3 * np.eye(2)
+    # the rectangle is off-image, so the record is culled: check via a copy
+    # whose mean sits on-image but shares the clamped Jacobian is impossible;
+    # instead compare the radius decision distance, which is reported anyway.
+    mid = 0.5 * (C[0, 0] + C[1, 1])
+    det = C[0, 0] * C[1, 1] - C[0, 1] ** 2
+    lam = mid + math.sqrt(max(0.1, mid * mid - det))
+    rr = 3 * math.sqrt(lam)
+    assert abs(pre["rad_dist"][0] - abs(rr - round(rr))) < 1e-9
+    assert pre["tiles"][0] == 0  # 3 tan(fov) off-axis: outside the image
+
+
+def test_quaternion_norm_is_irrelevant(oracle):
+    """Quaternions are normalised before use: scaling them by a power of two
+    (exact in float32, and exact through the normalisation) changes nothing."""
+    sc, cam = tiny_scene(200, 12, 40, 40)
+    pre = oracle.preprocess(sc, cam)
+    sc.quats *= np.float32(4.0)
+    pre2 = oracle.preprocess(sc, cam)
+    assert np.array_equal(pre2["cov2d"], pre["cov2d"])
+
+
+def test_near_plane_and_offscreen_cull(oracle):
+    sc, cam = tiny_scene(400, 5, 48, 40, near_frac=0.25, spill=2.5)
+    pre = oracle.preprocess(sc, cam)
+    near = pre["depth32"] <= np.float32(0.2)
+    assert near.sum() > 50
+    assert np.all(pre["radius"][near] == 0) and np.all(pre["tiles"][near] == 0)
+    off = (~near) & (pre["tiles"] == 0)
+    assert off.sum() > 10  # spill puts some fully off-image
+    vis = pre["tiles"] > 0
+    assert pre["visible"] == vis.sum()
+    assert np.all(pre["radius"][vis] > 0)
+    # the FP32 sort-key depth is within 2 ulp of the FP64 depth
+    d32 = pre["depth32"][vis].astype(np.float64)
+    ulp = np.spacing(pre["depth32"][vis]).astype(np.float64)
+    assert np.all(np.abs(d32 - pre["depth"][vis]) <= 2 * ulp)
+
+
+def test_rect_brute_force(oracle):
+    """The tile rectangle is [floor((x - r) / 16), floor((x + r + 15) / 16))
+    per axis, clamped to the tile grid, and tiles_touched is its area; every
+    tile it holds lies within the 3-sigma box widened by one tile."""
+    sc, cam = tiny_scene(300, 6, 77, 45, spill=1.6, log_scale=(-3.0, 0.8))
+    pre = oracle.preprocess(sc, cam)
+    for g in np.nonzero(pre["tiles"])[0]:
+        x, y = pre["xy"][g]
+        r = pre["radius"][g]
+        x0, y0, x1, y1 = pre["rect"][g]
+        for tx in range(cam.tiles_x):
+            want = max(0, math.floor((x - r) / 16)) <= tx < min(cam.tiles_x, math.floor((x + r + 15) / 16))
+            assert (x0 <= tx < x1) == want
+            if x0 <= tx < x1:
+                assert 16 * tx + 16 > x - r and 16 * tx <= x + r
+        for ty in range(cam.tiles_y):
+            want = max(0, math.floor((y - r) / 16)) <= ty < min(cam.tiles_y, math.floor((y + r + 15) / 16))
+            assert (y0 <= ty < y1) == want
+        assert pre["tiles"][g] == (x1 - x0) * (y1 - y0)
+
+
+# --------------------------------------------------------------------------
+# Blending: the paper's printed thresholds and the compositing identities
+# --------------------------------------------------------------------------
+
+def stack_scene(opacities, rgb=0.8, s=-3.0):
+    """Gaussians on the optical axis at increasing depth (front first)."""
+    n = len(opacities)
+    means = [[0.0, 0.0, 2.0 + 0.01 * i] for i in range(n)]
+    logits = [math.log(o / (1 - o)) for o in opacities]
+    return one_scene(means, [[s] * 3] * n, [[1, 0, 0, 0]] * n, logits, [[dc_for_rgb(rgb)] * 3] * n)
+
+
+def centre(img, key="color"):
+    a = img[key]
+    return a[..., 16, 16]
+
+
+def test_alpha_clamp_at_paper_value(oracle):
+    k = paper_constants()
+    cam = pinhole_camera(33, 33)
+    sc = stack_scene([0.99995])
+    pre, srt, img = oracle.frame(sc, cam)
+    assert abs(centre(img, "final_T") - (1 - k["alpha_max"])) < 1e-15
+    rgb = pre["rgb"][0, 0]
+    assert abs(centre(img)[0] - k["alpha_max"] * rgb) < 1e-15
+
+
+def test_alpha_skip_below_paper_threshold(oracle):
+    k = paper_constants()
+    cam = pinhole_camera(33, 33)
+    lo = stack_scene([k["alpha_min"] * 0.999])
+    hi = stack_scene([k["alpha_min"] * 1.001])
+    _, _, img_lo = oracle.frame(lo, cam)
+    _, _, img_hi = oracle.frame(hi, cam)
+    assert centre(img_lo, "final_T") == 1.0 and centre(img_lo, "n_contrib") == 0
+    assert centre(img_hi, "final_T") < 1.0 and centre(img_hi, "n_contrib") == 1
+
+
+def test_stop_rule_closed_form(oracle):
+    """alpha = 0.95 repeatedly: T = 0.05, 0.0025, 1.25e-4, then the 4th would
+    leave 6.25e-6 < 1e-4, so it is not blended and the pixel stops for good,
+    even though later Gaussians (alpha 0.005) would keep T above 1e-4."""
+    k = paper_constants()
+    cam = pinhole_camera(33, 33)
+    ops = [0.95] * 4 + [0.005] * 296
+    sc = stack_scene(ops)
+    pre, srt, img = oracle.frame(sc, cam)
+    o = 1 / (1 + math.exp(-float(np.float32(math.log(0.95 / 0.05)))))
+    T = 1.0
+    blended = 0
+    for _ in range(3):
+        assert T * (1 - o) >= k["t_stop"]
+        T *= 1 - o
+        blended += 1
+    assert T * (1 - o) < k["t_stop"]
+    assert centre(img, "n_contrib") == 3
+    assert abs(centre(img, "final_T") - T) < 1e-15
+    rgb = pre["rgb"][0, 0]
+    assert abs(centre(img)[0] - rgb * (1 - T)) < 1e-13
+    assert centre(img, "n_eval") == 4
+
+
+def test_n_contrib_counts_skipped(oracle):
+    """n_contrib is the 1-based list position of the last blended Gaussian,
+    skipped ones included."""
+    cam = pinhole_camera(33, 33)
+    sc = stack_scene([0.002, 0.5, 0.001, 0.001])
+    _, _, img = oracle.frame(sc, cam)
+    assert centre(img, "n_contrib") == 2
+
+
+def test_white_splats_out_equals_one_minus_T(oracle):
+    """All colours 1 and black background: C = sum alpha_i T_i = 1 - T_final
+    (the blend telescopes), and T is within [1e-4, 1]."""
+    sc, cam = tiny_scene(2000, 7, 64, 48, log_scale=(-2.8, 0.5), opacity_std=2.0)
+    sc.sh[:] = 0
+    sc.sh[:, 0, :] = dc_for_rgb(1.0)
+    pre, srt, img = oracle.frame(sc, cam)
+    for ch in range(3):
+        np.testing.assert_allclose(img["color"][ch], 1 - img["final_T"], atol=1e-12)
+    assert img["final_T"].min() >= 1e-4 and img["final_T"].max() <= 1.0
+    assert (img["final_T"] < 0.01).mean() > 0.05  # the scene does saturate
+
+
+def test_background_enters_as_T_bg(oracle):
+    sc, cam = tiny_scene(300, 8, 40, 40)
+    bg = (0.25, 0.5, 1.0)
+    pre, srt, img0 = oracle.frame(sc, cam)
+    img1 = oracle.render(pre, srt, cam, bg)
+    for ch in range(3):
+        np.testing.assert_allclose(img1["color"][ch] - img0["color"][ch], bg[ch] * img0["final_T"], atol=1e-14)
+
+
+def test_permutation_invariance(oracle):
+    sc, cam = tiny_scene(500, 9, 64, 48)
+    perm = np.random.default_rng(1).permutation(sc.n)
+    _, _, a = oracle.frame(sc, cam)
+    _, _, b = oracle.frame(subset_scene(sc, perm), cam)
+    assert np.array_equal(a["color"], b["color"]) and np.array_equal(a["n_contrib"], b["n_contrib"])
+
+
+@pytest.mark.parametrize("seed,w,h", [(1, 61, 37), (2, 48, 48), (3, 17, 90), (4, 100, 20)])
+def test_tiled_equals_bruteforce(oracle, seed, w, h):
+    """Tile lists + sort + ranges give exactly the per-pixel result of
+    sorting, for each pixel, every Gaussian whose rectangle holds its tile."""
+    sc, cam = tiny_scene(250, seed, w, h, near_frac=0.05, spill=1.3, log_scale=(-3.0, 0.7))
+    pre, srt, img = oracle.frame(sc, cam, bg=(0.1, 0.2, 0.3))
+    bf = oracle.render_bruteforce(pre, cam, bg=(0.1, 0.2, 0.3))
+    for k in ("color", "final_T", "n_contrib", "n_eval"):
+        assert np.array_equal(img[k], bf[k]), k
+
+
+def test_unrestricted_bruteforce_difference_reported(oracle):
+    """Without the 3-sigma rectangle restriction some pixels change: the
+    rectangle truncates contributions.  Reported, not asserted."""
+    sc, cam = tiny_scene(250, 1, 61, 37, log_scale=(-3.0, 0.7))
+    pre, srt, img = oracle.frame(sc, cam)
+    bf = oracle.render_bruteforce(pre, cam, use_rect=False)
+    diff = np.abs(img["color"] - bf["color"]).max()
+    print(f"max |tiled - unrestricted| = {diff:.3e}")
+    assert np.isfinite(diff)
+
+
+# --------------------------------------------------------------------------
+# Keys, sort and ranges
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,w,h", [(1, 61, 37), (5, 96, 80)])
+def test_keys_and_ranges_brute_force(oracle, seed, w, h):
+    sc, cam = tiny_scene(300, seed, w, h, near_frac=0.05, log_scale=(-3.0, 0.7))
+    pre = oracle.preprocess(sc, cam)
+    srt = oracle.duplicate_sort(pre, cam)
+    keys, vals, ranges = srt["keys"], srt["vals"], srt["ranges"]
+    # brute force: every (tile, gid) pair with the tile inside the rectangle
+    pairs = []
+    for g in range(sc.n):
+        x0, y0, x1, y1 = pre["rect"][g]
+        if pre["tiles"][g] == 0:
+            continue
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                pairs.append((ty * cam.tiles_x + tx, pre["depth32"][g].view(np.uint32), g))
+    pairs.sort(key=lambda p: (p[0], p[1], p[2]))
+    assert srt["m"] == len(pairs) == pre["tiles"].sum()
+    want_keys = np.array([(np.uint64(t) << np.uint64(32)) | np.uint64(d) for t, d, _ in pairs], np.uint64)
+    assert np.array_equal(keys, want_keys)
+    assert np.array_equal(vals, np.array([g for _, _, g in pairs], np.uint32))
+    tile_of = (keys >> np.uint64(32)).astype(np.int64)
+    for t in range(cam.num_tiles):
+        s, e = ranges[t]
+        sel = np.nonzero(tile_of == t)[0]
+        if len(sel) == 0:
+            assert s == 0 and e == 0
+        else:
+            assert s == sel[0] and e == sel[-1] + 1
+    assert int((ranges[:, 1].astype(np.int64) - ranges[:, 0]).sum()) == srt["m"]
+
+
+def test_config1_workload_shape(oracle):
+    """The 16k-Gaussian 256x256 frame: counts are stable across runs."""
+    sc = uniform_box_scene(16384, seed=0)
+    cam = pinhole_camera(256, 256, 60.0)
+    pre, srt, img = oracle.frame(sc, cam)
+    assert pre["visible"] > 16000
+    assert srt["m"] == pre["tiles"].sum()
+    assert img["n_eval"].sum() > 1_000_000
+    assert np.all(img["final_T"] >= 1e-4)

@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Frames/s of the full 3D Gaussian splatting forward pass (preprocess ->
+duplicate keys -> radix sort -> tile ranges -> tile render) on synthetic
+scenes, with per-kernel roofline fractions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+
+One step renders one frame of the workload (default: 3M Gaussians at
+1600x1064, poses cycled over a 20-pose orbit).  Under torchrun each rank
+renders its own poses of a replica of the scene (no data-path collective);
+the timed region is bracketed by a barrier and a device synchronisation and
+the max over ranks is reported.  Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s at 3M Gaussians 1600x1064 vs roofline; served p50/p99 latency"
+FLOP_PER_EVAL = 25  # FP32 work per Gaussian-pixel evaluation of the blend (FMA = 2)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["gs", "reference"], default="gs")
+    p.add_argument("--workload", default="fwd_3m_1600x1064")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+def oracle_frame_sample(scene, cam, rows_tiles: int, threads: int = 0):
+    """The FP64 oracle on one frame: full preprocess and sort, then
+    ``rows_tiles`` tile rows of the render; returns timings and the
+    extrapolated seconds per full frame."""
+    from oracle import oracle as O
+    O.build_oracle()
+    t0 = time.perf_counter()
+    pre = O.preprocess(scene, cam)
+    t1 = time.perf_counter()
+    srt = O.duplicate_sort(pre, cam)
+    t2 = time.perf_counter()
+    ty = cam.tiles_y
+    band0 = max(0, ty // 2 - rows_tiles // 2)
+    rows = (16 * band0, min(cam.height, 16 * (band0 + rows_tiles)))
+    img = O.render(pre, srt, cam, rows=rows, threads=threads)
+    t3 = time.perf_counter()
+    frac = (rows[1] - rows[0]) / cam.height
+    sec_frame = (t1 - t0) + (t2 - t1) + (t3 - t2) / frac
+    cores = os.cpu_count() if (O.has_openmp() and threads <= 0) else max(threads, 1)
+    return dict(pre_s=t1 - t0, sort_s=t2 - t1, render_band_s=t3 - t2, band_rows=rows, frac=frac,
+                sec_per_frame=sec_frame, cores=cores, m=srt["m"])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synth import CONFIGS
+    wl = CONFIGS[args.workload]
+    scene = wl["scene"]()
+    cams = wl["cameras"]()
+    times, samples = [], []
+    for k in range(args.warmup + args.steps):
+        cam = cams[k % len(cams)]
+        t = time.perf_counter()
+        s = oracle_frame_sample(scene, cam, rows_tiles=1)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+            samples.append(s)
+    fps = 1.0 / statistics.mean(s["sec_per_frame"] for s in samples)
+    cores = samples[0]["cores"]
+    line = dict(
+        metric=METRIC, value=fps, unit="frames/s", impl="reference", n_gpus=args.gpus, steps=args.steps,
+        warmup=args.warmup, ms_per_step=1000.0 * statistics.mean(times), higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=args.workload, gaussians=scene.n, width=cams[0].width, height=cams[0].height,
+                    poses=len(cams)),
+        cpu_baseline=dict(value=fps, unit="frames/s", cores=cores, kind="oracle",
+                          sample="per step: FP64 oracle preprocess + duplicate/sort of a whole frame and one "
+                                 "16-pixel tile row of its render, extrapolated to the full frame"),
+        e2e=dict(value=fps, unit="frames/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+    )
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group(backend="nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    if rank == 0:
+        from paper_2509_25626_gb300 import build
+        build.build()
+    barrier()
+    import paper_2509_25626_gb300 as gs
+    from synth import CONFIGS
+
+    wl = CONFIGS[args.workload]
+    scene = wl["scene"]()
+    cams = wl["cameras"]()
+    P = len(cams)
+    st = gs.SceneTensors.from_scene(scene, dev)
+    n = scene.n
+    W, H = cams[0].width, cams[0].height
+    T = gs.num_tiles(cams[0])
+
+    # instance counts per pose (untimed; sizes the key buffers)
+    ms = []
+    probe_cap = 1 << 24
+    for cam in cams:
+        sp = gs.preprocess(st, cam)
+        while True:
+            try:
+                _, _, _, m, _ = gs.sort(sp, n, cam, probe_cap)
+                break
+            except gs.GsError as e:
+                if e.code != gs.GS_ERR_CAPACITY:
+                    raise
+                probe_cap *= 2
+        ms.append(m)
+        del sp
+    torch.cuda.empty_cache()
+    m_cap = int(max(ms) * 1.05) + 4096
+    r = gs.Renderer(n, W, H, m_cap, dev)
+
+    # evaluations per pose (untimed), the render's work count
+    evals = []
+    for cam in cams:
+        gs.preprocess(st, cam, r.splats)
+        gs.sort(r.splats, n, cam, m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
+        _, _, _, ne = gs.render_workload(r.splats, r.vals, r.ranges, cam)
+        evals.append(int(ne.to(torch.int64).sum().item()))
+    vis = []
+    for cam in cams[:1]:
+        gs.preprocess(st, cam, r.splats)
+        vis.append(int((r.splats.view(torch.int32)[:, 11] > 0).sum().item()))
+
+    stream = torch.cuda.current_stream(dev)
+    pose_of = lambda k: (k * world + rank) % P
+
+    for k in range(args.warmup):
+        r.frame(st, cams[pose_of(k)])
+    torch.cuda.synchronize(dev)
+
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    ev = [[E() for _ in range(4)] for _ in range(args.steps)]
+    start, end = E(), E()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    start.record(stream)
+    for k in range(args.steps):
+        cam = cams[pose_of(args.warmup + k)]
+        e = ev[k]
+        e[0].record(stream)
+        gs.preprocess(st, cam, r.splats)
+        e[1].record(stream)
+        gs.sort(r.splats, n, cam, m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
+        e[2].record(stream)
+        gs.render(r.splats, r.vals, r.ranges, cam, (0.0, 0.0, 0.0), r.image, r.final_T, r.n_contrib)
+        e[3].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier()
+    t_ms = start.elapsed_time(end)
+    pre_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    sort_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    rend_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
+    m_last, over = r.instances()
+    assert not over, "instance capacity overflow during the timed region"
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    fps = args.steps * world / (t_ms / 1000.0)
+
+    # end to end through the public API: scene from pinned host memory each
+    # step, image back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in scene.arrays()]
+        himg = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+        h2d = sum(h.numel() * h.element_size() for h in host)
+        d2h = himg.numel() * himg.element_size()
+        dst = [st.means, st.log_scales, st.quats, st.opacity_logits, st.sh]
+        for k in range(2):
+            for d_, h_ in zip(dst, host):
+                d_.copy_(h_, non_blocking=True)
+            r.frame(st, cams[pose_of(k)])
+            himg.copy_(r.image, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        barrier()
+        s2, e2 = E(), E()
+        s2.record(stream)
+        for k in range(args.steps):
+            for d_, h_ in zip(dst, host):
+                d_.copy_(h_, non_blocking=True)
+            r.frame(st, cams[pose_of(k)])
+            himg.copy_(r.image, non_blocking=True)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        te = s2.elapsed_time(e2)
+        if world > 1:
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = dict(value=args.steps * world / (te / 1000.0), unit="frames/s", h2d_bytes_per_step=h2d,
+                   d2h_bytes_per_step=d2h)
+
+    # roofline of the dominant kernel (the render: FP32 issue bound)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s at the max SM clock
+    used = [pose_of(args.warmup + k) for k in range(args.steps)]
+    evals_mean = statistics.mean(evals[p] for p in used)
+    ms_mean = statistics.mean(ms[p] for p in used)
+    render_tflops = evals_mean * FLOP_PER_EVAL / (rend_ms / 1000.0) / 1e12
+    pre_bytes = n * (236 + 64)
+    pre_gbs = pre_bytes / (pre_ms / 1000.0) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "render_traffic.json")) as f:
+            tr = json.load(f)
+        if tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_sha("render.cu"):
+            traffic = tr.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roofline = dict(bound="alu", achieved=render_tflops, peak=fp32_peak, unit="TFLOP/s",
+                    frac=render_tflops / fp32_peak, traffic=traffic,
+                    kernel="render", work=f"{evals_mean:.4g} Gaussian-pixel evaluations x {FLOP_PER_EVAL} FLOP",
+                    peak_src=f"{sms} SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = render_tflops / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+    kernels = dict(
+        preprocess=dict(ms=pre_ms, bytes=pre_bytes, gbs=pre_gbs, frac_hbm=pre_gbs / peaks["hbm_gbs"]),
+        sort=dict(ms=sort_ms, instances=ms_mean),
+        render=dict(ms=rend_ms, evals=evals_mean, tflops=render_tflops),
+    )
+    tb = max(0, math.ceil(math.log2(T))) if T > 1 else 0
+    launches_per_frame = 1 + 17 + 2 + 3 * ((tb + 7) // 8) + 1
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_frame_sample(scene, cams[used[0]], rows_tiles=args.cpu_rows)
+        cpu = dict(value=1.0 / s["sec_per_frame"], unit="frames/s", cores=s["cores"], kind="oracle",
+                   sample=f"one frame (pose {used[0]}): FP64 oracle preprocess ({s['pre_s']:.2f} s) and "
+                          f"duplicate/sort ({s['sort_s']:.2f} s) in full, render of pixel rows {s['band_rows']} "
+                          f"({s['render_band_s']:.2f} s) extrapolated to the whole image")
+
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=fps, unit="frames/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32", data="synthetic",
+            config=dict(workload=args.workload, gaussians=n, width=W, height=H, poses=P, tiles=T,
+                        instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
+                        m_cap=m_cap, parallelism=f"replicas{world}",
+                        l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
+            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
+            gpu_launches=launches_per_frame * args.steps, clocks=clocks,
+            peaks_src=peaks["src"],
+        )
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_sha(name: str) -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2509_25626_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) 3D Gaussian splatting hot path.
+ *
+ * The forward pass follows the pipeline of Section II-B of "LLM-Powered Code
+ * Analysis and Optimization for Gaussian Splatting Kernels" (arXiv
+ * 2509.25626): (1) preprocessing -- cull, project each 3D Gaussian to a 2D
+ * splat with colour and depth, replicate it for every 16x16 pixel tile it
+ * touches, sort the replicas by depth within each tile; (2) alpha blending --
+ * per-tile ranges, then one thread block per tile blends its splats front to
+ * back (Eq. 1, Algorithm 1).
+ *
+ *   gs_preprocess   per-Gaussian projection, colour, radius, tile rectangle
+ *   gs_sort         key duplication, radix sort, per-tile ranges
+ *   gs_render       per-tile front-to-back alpha blending
+ *
+ * Conventions shared by every call:
+ *   - Every pointer argument named as device memory must point to memory of
+ *     the current CUDA device.  The caller owns every buffer and the stream;
+ *     the library allocates nothing and keeps no state between calls.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls only enqueue work (no host synchronisation)
+ *     unless stated otherwise.
+ *   - Return value: GS_OK (0) or a negative GS_ERR_* code.  Argument checks
+ *     happen before any launch; a launch failure returns GS_ERR_CUDA and
+ *     gs_last_cuda_error() names the CUDA error.  No C++ exception crosses
+ *     this boundary.
+ *   - Pixel (px, py) has its centre at integer coordinates; images are
+ *     row-major, channel-major for colour ([3][H][W]).
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_TILE 16 /* tile edge in pixels (Section II-B: default 16 x 16) */
+
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1, /* null/misaligned pointer, bad size or camera */
+    GS_ERR_CAPACITY = -2,    /* more tile instances than the key buffers hold */
+    GS_ERR_CUDA = -3,        /* a CUDA launch or runtime call failed */
+    GS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+};
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  Host memory. */
+typedef struct gs_camera {
+    float viewmat[16];   /* world -> camera, row-major 4x4; last row 0 0 0 1 */
+    float fx, fy;        /* focal lengths in pixels */
+    float cx, cy;        /* principal point in pixels */
+    int32_t width;       /* image size in pixels, 1 .. 65535 * 16 */
+    int32_t height;
+    float tan_fovx;      /* tan(half field of view); the EWA Jacobian is */
+    float tan_fovy;      /* evaluated inside 1.3 x these (3DGS frustum slack) */
+} gs_camera;
+
+/* Scene parameters: float32 structure-of-arrays in device memory, each array
+ * 16-byte aligned.  n may be 0. */
+typedef struct gs_scene {
+    const float *means;          /* [n][3] world-space centres */
+    const float *log_scales;     /* [n][3] log standard deviations per axis */
+    const float *quats;          /* [n][4] rotation (w, x, y, z), any norm > 0 */
+    const float *opacity_logits; /* [n] opacity = sigmoid(logit) */
+    const float *sh;             /* [n][16][3] SH coefficients, RGB-minor */
+    int64_t n;
+    int32_t sh_degree;           /* 0 .. 3 bands used (the array is always 16) */
+    int32_t reserved;
+} gs_scene;
+
+/* One projected Gaussian ("splat"), written by gs_preprocess: 64 bytes.
+ * The 2D covariance Sigma' = J W Sigma W^T J^T + 0.3 I is stored through an
+ * upper-triangular factor of its inverse, scaled so that for d = (x, y) - p
+ *     -0.5 d^T Sigma'^-1 d * log2(e) = -(u*u + v*v),
+ *     u = w00 dx + w01 dy,   v = w11 dy,
+ * and alpha = min(0.99, 2^(log2_opacity - u*u - v*v)).
+ * A culled Gaussian has radius = 0 and tiles_touched = 0. */
+typedef struct gs_splat {
+    float x, y;               /* pixel-space mean */
+    float w00, w01, w11;      /* inverse-covariance factor (see above) */
+    float log2_opacity;       /* log2(sigmoid(logit)) */
+    float r, g, b;            /* SH colour + 0.5, clamped at 0 */
+    float depth;              /* view-space z, FP32; its bits form the sort key */
+    int32_t radius;           /* ceil(3 sqrt(lambda_max(Sigma'))) pixels */
+    uint32_t tiles_touched;   /* (x1 - x0) (y1 - y0) */
+    uint32_t rect_lo;         /* x0 | y0 << 16, tile rectangle, inclusive */
+    uint32_t rect_hi;         /* x1 | y1 << 16, exclusive */
+    float opacity;            /* sigmoid(logit) */
+    float reserved;
+} gs_splat;
+
+/* Section II-B (1), projection step.  One thread per Gaussian:
+ *   z = V.[m, 1] (FP32, fmaf(V22, mz, fmaf(V21, my, fmaf(V20, mx, V23))));
+ *   cull if z <= 0.2;
+ *   Sigma = R(q) diag(exp(2 s)) R(q)^T;  J at the mean clamped to 1.3 tan(fov);
+ *   Sigma' = J W Sigma W^T J^T + 0.3 I;
+ *   radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
+ *   rect = [floor((p - r) / 16), floor((p + r + 15) / 16)) clamped to the grid; cull if empty;
+ *   colour = max(sum_lm c_lm Y_lm(dir) + 0.5, 0), dir from the camera centre to the mean.
+ * scene: device arrays; cam: host struct; splats: device, [scene->n] records,
+ * 16-byte aligned.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, void *stream);
+
+/* Bytes of device workspace gs_sort needs for n Gaussians, m_cap tile
+ * instances and num_tiles = ceil(W/16) * ceil(H/16) tiles (>= 256-byte
+ * aligned by the caller). */
+size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles);
+
+/* Section II-B: replicate every visible splat for each tile of its
+ * rectangle with key (tile_id << 32 | float_bits(depth)), tile_id =
+ * ty * ceil(W/16) + tx, value = Gaussian id; sort stably by key (ties keep
+ * ascending id); ranges[t] = [start, end) of tile t's instances in the sorted
+ * list, [0, 0) for an empty tile (Algorithm 1, "load work range").
+ *
+ * splats: device, [n] records from gs_preprocess with the same camera.
+ * keys, vals: device, capacity m_cap each (8- and 4-byte elements, 16-byte
+ * aligned); on return the first M entries hold the sorted instances.
+ * ranges: device, [num_tiles][2] uint32.
+ * workspace: device, gs_sort_workspace_bytes(n, m_cap, num_tiles) bytes.
+ * m_out: HOST pointer or NULL.  If non-NULL the call synchronises the stream
+ * once to read M, stores it, and returns GS_ERR_CAPACITY (having written
+ * nothing else) when M > m_cap.  If NULL the call never synchronises: M
+ * stays on the device, an overflow is recorded there, only the first m_cap
+ * instances are sorted, and gs_sort_status() reports it later.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
+int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *keys, uint32_t *vals,
+            int64_t m_cap, uint32_t *ranges, void *workspace, size_t workspace_bytes, int64_t *m_out,
+            void *stream);
+
+/* Read back the device-side instance count and overflow flag of the last
+ * gs_sort that used `workspace` (synchronises `stream`).  m_out: host, the
+ * true M (which may exceed m_cap).  Returns GS_OK or GS_ERR_CAPACITY. */
+int gs_sort_status(const void *workspace, int64_t *m_out, void *stream);
+
+/* Section II-B (2), Algorithm 1, Eq. 1: one 16x16 thread block per tile walks
+ * ranges[tile] of the sorted values front to back; per pixel p and splat g:
+ *   alpha = min(0.99, o_g exp(-0.5 d^T Sigma'^-1 d)), d = (x_g, y_g) - p;
+ *   skip if alpha < 1/255; stop (without blending g) once T (1 - alpha) < 1e-4;
+ *   C += rgb_g alpha T; T *= 1 - alpha.
+ * Writes out_color[c][py][px] = C_c + T bg_c, final_T[py][px] = T and
+ * n_contrib[py][px] = 1-based list position of the last blended splat.
+ * splats, vals, ranges: device inputs from gs_preprocess / gs_sort; bg: host
+ * float[3]; out_color [3][H][W], final_T [H][W], n_contrib [H][W]: device,
+ * 4-byte elements.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+              const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream);
+
+/* gs_render plus, per pixel, the number of splats evaluated before the
+ * pixel stopped (the stopping splat included; all of the tile's splats if it
+ * never stopped): n_eval [H][W] uint32, device.  Its sum over the image is
+ * the "Gaussian-pixel evaluations" work count, the per-thread workload
+ * measure of the paper's Table III.  Slightly slower than gs_render; meant
+ * for workload characterisation, not for the hot path.
+ * Errors: as gs_render. */
+int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                       const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
+                       void *stream);
+
+/* Text for a GS_* code, or the CUDA error string of the last GS_ERR_CUDA. */
+const char *gs_strerror(int code);
+const char *gs_last_cuda_error(void);
+
+/* Library version and the compute capability it was built for (e.g. 103). */
+int gs_version(void);
+int gs_built_arch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

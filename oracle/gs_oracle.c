@@ -173,6 +173,9 @@ int64_t oracle_preprocess(int64_t n, const float *means, const float *log_scales
         for (int j = 0; j < 3; ++j) campos[i] -= cam.V[j][i] * cam.V[j][3];
     }
     int64_t visible = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static, 4096) reduction(+ : visible)
+#endif
     for (int64_t g = 0; g < n; ++g) {
         const float *mf = means + 3 * g;
         double m[3] = {mf[0], mf[1], mf[2]};
@@ -262,11 +265,12 @@ int64_t oracle_preprocess(int64_t n, const float *means, const float *log_scales
         double d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
         double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int k = 0; k < 3; ++k) d[k] /= dn;
+        double Y[16];
+        for (int l = 0; l <= sh_degree; ++l)
+            for (int mm = -l; mm <= l; ++mm) Y[l * l + l + mm] = oracle_sh_basis(l, mm, d[0], d[1], d[2]);
         for (int ch = 0; ch < 3; ++ch) {
             double acc = 0.0;
-            for (int l = 0; l <= sh_degree; ++l)
-                for (int mm = -l; mm <= l; ++mm)
-                    acc += (double)sh[(g * 16 + (l * l + l + mm)) * 3 + ch] * oracle_sh_basis(l, mm, d[0], d[1], d[2]);
+            for (int k = 0; k < (sh_degree + 1) * (sh_degree + 1); ++k) acc += (double)sh[(g * 16 + k) * 3 + ch] * Y[k];
             rgb[3 * g + ch] = fmax(acc + 0.5, 0.0);
         }
 

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) CUDA implementation of the 3D Gaussian splatting forward
+hot path: preprocess -> duplicate keys -> radix sort -> tile ranges ->
+per-tile alpha blending, behind the C ABI in include/gs.h (libgs.so).
+"""
+
+from ._lib import GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_INVALID_ARG, GS_OK, SPLAT_DTYPE, GsError  # noqa: F401
+from .api import (  # noqa: F401
+    Renderer,
+    SceneTensors,
+    camera_struct,
+    num_tiles,
+    preprocess,
+    render,
+    render_workload,
+    sort,
+    sort_status,
+    sort_workspace_bytes,
+)

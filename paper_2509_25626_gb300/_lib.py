@@ -1,0 +1,94 @@
+"""ctypes view of the C ABI in include/gs.h.
+
+Loads the in-tree libgs.so.  There is no fallback: if the library is missing
+or fails to load, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs.so")
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = -1
+GS_ERR_CAPACITY = -2
+GS_ERR_CUDA = -3
+GS_ERR_TIMEOUT = -4
+
+c_float, c_int32, c_int64, c_void_p, c_size_t = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                                 ctypes.c_size_t)
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("viewmat", c_float * 16), ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
+                ("width", c_int32), ("height", c_int32), ("tan_fovx", c_float), ("tan_fovy", c_float)]
+
+
+class GsScene(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
+                ("sh", c_void_p), ("n", c_int64), ("sh_degree", c_int32), ("reserved", c_int32)]
+
+
+# numpy view of one gs_splat record (64 bytes)
+SPLAT_DTYPE = np.dtype([
+    ("x", "<f4"), ("y", "<f4"), ("w00", "<f4"), ("w01", "<f4"), ("w11", "<f4"), ("log2_opacity", "<f4"),
+    ("r", "<f4"), ("g", "<f4"), ("b", "<f4"), ("depth", "<f4"), ("radius", "<i4"), ("tiles_touched", "<u4"),
+    ("rect_lo", "<u4"), ("rect_hi", "<u4"), ("opacity", "<f4"), ("reserved", "<f4"),
+])
+assert SPLAT_DTYPE.itemsize == 64
+
+
+class GsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2509_25626_gb300.build` "
+                               "(or __graft_entry__.build()) on a machine with nvcc")
+        L = ctypes.CDLL(LIB_PATH)
+        P = c_void_p
+        L.gs_preprocess.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P]
+        L.gs_sort_workspace_bytes.argtypes = [c_int64, c_int64, c_int32]
+        L.gs_sort_workspace_bytes.restype = c_size_t
+        L.gs_sort.argtypes = [P, c_int64, ctypes.POINTER(GsCamera), P, P, c_int64, P, P, c_size_t,
+                              ctypes.POINTER(c_int64), P]
+        L.gs_sort_status.argtypes = [P, ctypes.POINTER(c_int64), P]
+        L.gs_render.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P]
+        L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P]
+        L.gs_strerror.argtypes = [ctypes.c_int]
+        L.gs_strerror.restype = ctypes.c_char_p
+        L.gs_last_cuda_error.restype = ctypes.c_char_p
+        for name in ("gs_preprocess", "gs_sort", "gs_sort_status", "gs_render", "gs_render_workload", "gs_version",
+                     "gs_built_arch"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().gs_strerror(int(code)).decode()
+
+
+def check(code: int, what: str) -> int:
+    if code != GS_OK:
+        raise GsError(code, what)
+    return code
+
+
+def exported_symbols():
+    """Names of the gs_* functions the header declares."""
+    return ["gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
+            "gs_render_workload", "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

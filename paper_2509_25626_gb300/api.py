@@ -1,0 +1,210 @@
+"""Thin torch-facing binding of the gs_* C ABI.
+
+Argument marshalling only: every step of the hot path runs in libgs.so.
+PyTorch supplies device memory and the current CUDA stream.  Tensors are
+passed as raw pointers; dtypes and shapes follow include/gs.h:
+
+    splats   float32 [n, 16]    one 64-byte gs_splat record per Gaussian
+    keys     int64   [m_cap]    (tile << 32 | depth bits), sorted
+    vals     int32   [m_cap]    Gaussian ids (uint32 bit patterns)
+    ranges   int32   [T, 2]     per-tile [start, end)
+    image    float32 [3, H, W], final_T float32 [H, W], n_contrib int32 [H, W]
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def camera_struct(cam) -> L.GsCamera:
+    """gs_camera from any object with viewmat, fx, fy, cx, cy, width, height,
+    tan_fovx, tan_fovy attributes."""
+    c = L.GsCamera()
+    vm = np.ascontiguousarray(np.asarray(cam.viewmat, np.float32).reshape(16))
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.tan_fovx, c.tan_fovy = float(cam.tan_fovx), float(cam.tan_fovy)
+    return c
+
+
+def num_tiles(cam) -> int:
+    return ((int(cam.width) + 15) // 16) * ((int(cam.height) + 15) // 16)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+def _check_tensor(t: torch.Tensor, dtype, name: str):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+
+
+@dataclass
+class SceneTensors:
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int = 3
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @classmethod
+    def from_arrays(cls, means, log_scales, quats, opacity_logits, sh, sh_degree=3, device="cuda"):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device).contiguous()
+        return cls(f(means), f(log_scales), f(quats), f(opacity_logits), f(sh), int(sh_degree))
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        return cls.from_arrays(scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
+                               scene.sh_degree, device)
+
+    def struct(self) -> L.GsScene:
+        for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            _check_tensor(getattr(self, name), torch.float32, name)
+        s = L.GsScene()
+        s.means, s.log_scales, s.quats = self.means.data_ptr(), self.log_scales.data_ptr(), self.quats.data_ptr()
+        s.opacity_logits, s.sh = self.opacity_logits.data_ptr(), self.sh.data_ptr()
+        s.n, s.sh_degree = self.n, int(self.sh_degree)
+        return s
+
+
+def preprocess(scene: SceneTensors, cam, splats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """gs_preprocess: returns float32 [n, 16] splat records."""
+    n = scene.n
+    if splats is None:
+        splats = torch.empty((max(n, 1), 16), dtype=torch.float32, device=scene.means.device)
+    _check_tensor(splats, torch.float32, "splats")
+    c = camera_struct(cam)
+    L.check(L.lib().gs_preprocess(ctypes.byref(scene.struct()), ctypes.byref(c), _ptr(splats), _stream(stream)),
+            "gs_preprocess")
+    return splats
+
+
+def sort_workspace_bytes(n: int, m_cap: int, tiles: int) -> int:
+    return int(L.lib().gs_sort_workspace_bytes(int(n), int(m_cap), int(tiles)))
+
+
+def sort(splats: torch.Tensor, n: int, cam, m_cap: int, keys=None, vals=None, ranges=None, workspace=None,
+         count: bool = True, stream=None):
+    """gs_sort.  With count=True the call synchronises once and returns M
+    (raising GsError(GS_ERR_CAPACITY) if M > m_cap); otherwise M stays on the
+    device and the return value's m is None."""
+    dev = splats.device
+    T = num_tiles(cam)
+    if keys is None:
+        keys = torch.empty(max(m_cap, 1), dtype=torch.int64, device=dev)
+    if vals is None:
+        vals = torch.empty(max(m_cap, 1), dtype=torch.int32, device=dev)
+    if ranges is None:
+        ranges = torch.empty((T, 2), dtype=torch.int32, device=dev)
+    need = sort_workspace_bytes(n, m_cap, T)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    for t, dt, nm in ((keys, torch.int64, "keys"), (vals, torch.int32, "vals"), (ranges, torch.int32, "ranges"),
+                      (workspace, torch.uint8, "workspace")):
+        _check_tensor(t, dt, nm)
+    c = camera_struct(cam)
+    m = ctypes.c_int64(-1)
+    code = L.lib().gs_sort(_ptr(splats), int(n), ctypes.byref(c), _ptr(keys), _ptr(vals), int(m_cap), _ptr(ranges),
+                           _ptr(workspace), workspace.numel(), ctypes.byref(m) if count else None, _stream(stream))
+    L.check(code, "gs_sort")
+    return keys, vals, ranges, (int(m.value) if count else None), workspace
+
+
+def sort_status(workspace: torch.Tensor, stream=None):
+    """(M, overflowed) of the last gs_sort on this workspace (synchronises)."""
+    m = ctypes.c_int64(-1)
+    code = L.lib().gs_sort_status(_ptr(workspace), ctypes.byref(m), _stream(stream))
+    if code not in (L.GS_OK, L.GS_ERR_CAPACITY):
+        L.check(code, "gs_sort_status")
+    return int(m.value), code == L.GS_ERR_CAPACITY
+
+
+def render(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
+           out_color=None, final_T=None, n_contrib=None, stream=None):
+    """gs_render: returns (image [3, H, W], final_T [H, W], n_contrib [H, W])."""
+    dev = splats.device
+    H, W = int(cam.height), int(cam.width)
+    if out_color is None:
+        out_color = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    if final_T is None:
+        final_T = torch.empty((H, W), dtype=torch.float32, device=dev)
+    if n_contrib is None:
+        n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    for t, dt, nm in ((out_color, torch.float32, "out_color"), (final_T, torch.float32, "final_T"),
+                      (n_contrib, torch.int32, "n_contrib")):
+        _check_tensor(t, dt, nm)
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    code = L.lib().gs_render(_ptr(splats), _ptr(vals), _ptr(ranges), ctypes.byref(c), bgc, _ptr(out_color),
+                             _ptr(final_T), _ptr(n_contrib), _stream(stream))
+    L.check(code, "gs_render")
+    return out_color, final_T, n_contrib
+
+
+def render_workload(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
+                    stream=None):
+    """gs_render_workload: (image, final_T, n_contrib, n_eval [H, W] int32)."""
+    dev = splats.device
+    H, W = int(cam.height), int(cam.width)
+    out_color = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    final_T = torch.empty((H, W), dtype=torch.float32, device=dev)
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    n_eval = torch.empty((H, W), dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    code = L.lib().gs_render_workload(_ptr(splats), _ptr(vals), _ptr(ranges), ctypes.byref(c), bgc,
+                                      _ptr(out_color), _ptr(final_T), _ptr(n_contrib), _ptr(n_eval), _stream(stream))
+    L.check(code, "gs_render_workload")
+    return out_color, final_T, n_contrib, n_eval
+
+
+class Renderer:
+    """Device buffers for rendering one scene size at one resolution.
+
+    ``frame`` enqueues preprocess, sort and render on the current stream
+    without any host synchronisation; ``instances`` reads the device-side M
+    of the last frame (and whether it overflowed ``m_cap``)."""
+
+    def __init__(self, n: int, width: int, height: int, m_cap: int, device="cuda"):
+        self.n, self.width, self.height, self.m_cap = int(n), int(width), int(height), int(m_cap)
+        T = ((self.width + 15) // 16) * ((self.height + 15) // 16)
+        dev = torch.device(device)
+        self.splats = torch.empty((max(self.n, 1), 16), dtype=torch.float32, device=dev)
+        self.keys = torch.empty(max(self.m_cap, 1), dtype=torch.int64, device=dev)
+        self.vals = torch.empty(max(self.m_cap, 1), dtype=torch.int32, device=dev)
+        self.ranges = torch.empty((T, 2), dtype=torch.int32, device=dev)
+        self.workspace = torch.empty(sort_workspace_bytes(self.n, self.m_cap, T), dtype=torch.uint8, device=dev)
+        self.image = torch.empty((3, self.height, self.width), dtype=torch.float32, device=dev)
+        self.final_T = torch.empty((self.height, self.width), dtype=torch.float32, device=dev)
+        self.n_contrib = torch.empty((self.height, self.width), dtype=torch.int32, device=dev)
+
+    def frame(self, scene: SceneTensors, cam, bg=(0.0, 0.0, 0.0), stream=None):
+        if scene.n != self.n or int(cam.width) != self.width or int(cam.height) != self.height:
+            raise ValueError("scene size or resolution differs from the Renderer's buffers")
+        preprocess(scene, cam, self.splats, stream)
+        sort(self.splats, self.n, cam, self.m_cap, self.keys, self.vals, self.ranges, self.workspace, count=False,
+             stream=stream)
+        render(self.splats, self.vals, self.ranges, cam, bg, self.image, self.final_T, self.n_contrib, stream)
+        return self.image, self.final_T, self.n_contrib
+
+    def instances(self, stream=None):
+        return sort_status(self.workspace, stream)

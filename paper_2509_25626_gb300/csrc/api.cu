@@ -1,0 +1,162 @@
+// C ABI entry points (include/gs.h): argument checks, then launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "sort_ws.h"
+
+#ifndef GS_BUILT_ARCH
+#define GS_BUILT_ARCH 0
+#endif
+
+namespace gs {
+
+cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat *out, cudaStream_t stream);
+cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, cudaStream_t st);
+cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
+                             uint32_t num_tiles, uint64_t *keys, uint32_t *vals, uint32_t *ranges, cudaStream_t st);
+cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
+                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
+                          uint32_t *n_eval, cudaStream_t stream);
+
+static thread_local char g_cuda_err[256] = "no CUDA error recorded";
+
+void set_cuda_error(cudaError_t e) {
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+namespace {
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool camera_ok(const gs_camera *c) {
+    if (!c) return false;
+    if (c->width < 1 || c->height < 1 || c->width > 65535 * kTile || c->height > 65535 * kTile) return false;
+    const float f[] = {c->fx, c->fy, c->cx, c->cy, c->tan_fovx, c->tan_fovy};
+    for (float v : f)
+        if (!std::isfinite(v)) return false;
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(c->viewmat[i])) return false;
+    return c->fx > 0.f && c->fy > 0.f && c->tan_fovx > 0.f && c->tan_fovy > 0.f;
+}
+
+uint64_t tiles_of(const gs_camera *c) {
+    return (uint64_t)((c->width + kTile - 1) / kTile) * (uint64_t)((c->height + kTile - 1) / kTile);
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GS_OK;
+    set_cuda_error(e);
+    return GS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, void *stream) {
+    if (!scene || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
+    if (scene->n < 0 || scene->n > (int64_t)UINT32_MAX || scene->sh_degree < 0 || scene->sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        const void *ptrs[] = {scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, splats};
+        for (const void *p : ptrs)
+            if (!p || !aligned(p, 16)) return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_preprocess(*scene, make_cam_params(*cam), splats, (cudaStream_t)stream));
+}
+
+size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles) {
+    (void)num_tiles;
+    return carve_sort_ws(nullptr, n, m_cap, nullptr);
+}
+
+int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *keys, uint32_t *vals, int64_t m_cap,
+            uint32_t *ranges, void *workspace, size_t workspace_bytes, int64_t *m_out, void *stream) {
+    if (!camera_ok(cam) || n < 0 || n > (int64_t)UINT32_MAX || m_cap < 0 || m_cap > (int64_t)UINT32_MAX)
+        return GS_ERR_INVALID_ARG;
+    const uint64_t num_tiles = tiles_of(cam);
+    if (num_tiles > (uint64_t)UINT32_MAX) return GS_ERR_INVALID_ARG;
+    if (!ranges || !aligned(ranges, 8) || !workspace || !aligned(workspace, 256)) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!splats || !aligned(splats, 16))) return GS_ERR_INVALID_ARG;
+    if (m_cap > 0 && (!keys || !vals || !aligned(keys, 16) || !aligned(vals, 16))) return GS_ERR_INVALID_ARG;
+    if (workspace_bytes < gs_sort_workspace_bytes(n, m_cap, (int32_t)num_tiles)) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    SortWs ws;
+    carve_sort_ws(static_cast<char *>(workspace), n, m_cap, &ws);
+    cudaError_t e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (m_out) {
+        uint64_t m = 0;
+        e = cudaMemcpyAsync(&m, &ws.hdr->m_total, sizeof(m), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        *m_out = (int64_t)m;
+        if (m > (uint64_t)m_cap) return GS_ERR_CAPACITY;
+    }
+    const int tiles_x = (cam->width + kTile - 1) / kTile;
+    return cuda_status(launch_sort_back(splats, n, ws, (uint64_t)m_cap, tiles_x, (uint32_t)num_tiles, keys, vals,
+                                        ranges, st));
+}
+
+int gs_sort_status(const void *workspace, int64_t *m_out, void *stream) {
+    if (!workspace || !aligned(workspace, 256) || !m_out) return GS_ERR_INVALID_ARG;
+    SortHeader h;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    *m_out = (int64_t)h.m_total;
+    return h.overflow ? GS_ERR_CAPACITY : GS_OK;
+}
+
+static int render_common(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                         const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
+                         uint32_t *n_eval, void *stream) {
+    if (!camera_ok(cam) || !bg || !ranges || !aligned(ranges, 8)) return GS_ERR_INVALID_ARG;
+    if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
+    if (!out_color || !final_T || !n_contrib || !aligned(out_color, 4) || !aligned(final_T, 4) ||
+        !aligned(n_contrib, 4))
+        return GS_ERR_INVALID_ARG;
+    if (!splats || !aligned(splats, 16) || !vals || !aligned(vals, 4)) return GS_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render(splats, vals, ranges, make_cam_params(*cam), bg, out_color, final_T, n_contrib,
+                                     n_eval, (cudaStream_t)stream));
+}
+
+int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+              const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream) {
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, stream);
+}
+
+int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                       const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
+                       void *stream) {
+    if (!n_eval || !aligned(n_eval, 4)) return GS_ERR_INVALID_ARG;
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, n_eval, stream);
+}
+
+const char *gs_strerror(int code) {
+    switch (code) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID_ARG: return "invalid argument (null or misaligned pointer, bad size or camera)";
+        case GS_ERR_CAPACITY: return "tile instances exceed the key buffer capacity";
+        case GS_ERR_CUDA: return g_cuda_err;
+        case GS_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown gs error code";
+    }
+}
+
+const char *gs_last_cuda_error(void) { return g_cuda_err; }
+
+int gs_version(void) { return 1; }
+
+int gs_built_arch(void) { return GS_BUILT_ARCH; }
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal definitions shared by the CUDA translation units of libgs.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;
+constexpr int kTilePixels = kTile * kTile;
+
+// Per-pixel blend rules printed by the paper's render kernels (Appendix B).
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTStop = 1e-4f;
+
+// Projection constants of the 3DGS preprocess the paper builds on.
+constexpr float kNearZ = 0.2f;          // near-plane cull
+constexpr float kDilation = 0.3f;       // low-pass added to the 2D covariance
+constexpr float kFrustumSlack = 1.3f;   // Jacobian evaluated inside 1.3 tan(fov)
+constexpr float kLambdaFloor = 0.1f;    // floor under the eigenvalue discriminant
+
+constexpr float kLog2e = 1.4426950408889634f;
+// sqrt(log2(e) / 2): folds the -1/2 of the Gaussian exponent and the change
+// of base to 2 into the inverse-covariance factor.
+constexpr float kWhiten = 0.8493218002880191f;
+
+// Camera as the kernels see it (kernel parameter, passed by value).
+struct CamParams {
+    float V[12];          // rows 0..2 of the world->camera matrix
+    float fx, fy, cx, cy;
+    float tan_fovx, tan_fovy;
+    float campos[3];      // camera centre in world space
+    int width, height, tiles_x, tiles_y;
+};
+
+// Host-side conversion; the camera centre -R^T t is formed in double.
+inline CamParams make_cam_params(const gs_camera &c) {
+    CamParams p;
+    for (int i = 0; i < 12; ++i) p.V[i] = c.viewmat[i];
+    p.fx = c.fx;
+    p.fy = c.fy;
+    p.cx = c.cx;
+    p.cy = c.cy;
+    p.tan_fovx = c.tan_fovx;
+    p.tan_fovy = c.tan_fovy;
+    for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) acc -= (double)c.viewmat[4 * j + i] * (double)c.viewmat[4 * j + 3];
+        p.campos[i] = (float)acc;
+    }
+    p.width = c.width;
+    p.height = c.height;
+    p.tiles_x = (c.width + kTile - 1) / kTile;
+    p.tiles_y = (c.height + kTile - 1) / kTile;
+    return p;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x a multiple
+// of 32, at most 1024).  `scratch` holds >= 33 words.  Returns the exclusive
+// prefix; *total receives the block sum.  Contains __syncthreads().
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *scratch, uint32_t *total) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (unsigned)o) inc += t;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nwarps ? scratch[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (unsigned)o) wi += t;
+        }
+        if (lane < nwarps) scratch[lane] = wi - w;
+        if (lane == 31) scratch[32] = wi;
+    }
+    __syncthreads();
+    uint32_t res = scratch[warp] + inc - v;
+    *total = scratch[32];
+    __syncthreads();
+    return res;
+}
+
+// Records the first CUDA error of a launch sequence.
+void set_cuda_error(cudaError_t e);
+
+}  // namespace gs

@@ -23,7 +23,7 @@ MUTANTS = {
                             "2.0 * (x * y + w * z), 2.0 * (x * z - w * y)},"),
     "jacobian_sign": ("-cam.fx * txc", "cam.fx * txc"),
     "colour_offset": ("fmax(acc + 0.5, 0.0)", "fmax(acc, 0.0)"),
-    "sh_index": ("(l * l + l + mm)", "(l * l + l - mm)"),
+    "sh_index": ("Y[l * l + l + mm]", "Y[l * l + l - mm]"),
     "stop_not_permanent": ("if (Tn < T_MIN) break;", "if (Tn < T_MIN) continue;"),
     "n_contrib_blended_only": ("last = contrib;", "last = contrib - (contrib > 1);"),
     "rect_max_bound": ("floor((px + r + TILE - 1) / TILE)", "floor((px + r + TILE) / TILE)"),

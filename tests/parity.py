@@ -117,7 +117,7 @@ def compare_preprocess(gpu: np.ndarray, pre: dict, cam) -> dict:
     assert np.all(rgb_err <= 2e-5), f"rgb error {rgb_err.max():.3e}"
     op_err = np.abs(gpu["opacity"].astype(np.float64) - pre["opacity"])[b]
     assert np.all(op_err <= 1e-6), f"opacity error {op_err.max():.3e}"
-    lg_err = np.abs(gpu["log2_opacity"].astype(np.float64) - np.log2(pre["opacity"][b]))
+    lg_err = np.abs(gpu["log2_opacity"][b].astype(np.float64) - np.log2(pre["opacity"][b]))
     assert np.all(lg_err <= 1e-5 * np.maximum(1.0, np.abs(np.log2(pre["opacity"][b])))), \
         f"log2 opacity error {lg_err.max():.3e}"
     return dict(n=len(pre["tiles"]), visible=int(vis_o.sum()), ambiguous=int(amb.sum()),

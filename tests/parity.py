@@ -130,9 +130,8 @@ def compare_images(img: np.ndarray, final_T: np.ndarray, n_contrib: np.ndarray, 
     """GPU image vs oracle: 2e-4 absolute on every pixel except those where a
     near-threshold decision could move the value by more than half the
     tolerance; n_contrib exact where no decision was near."""
-    amb = ora["flip_impact"] > IMAGE_ATOL / 2
-    if exclude is not None:
-        amb = amb | exclude
+    near_amb = ora["flip_impact"] > IMAGE_ATOL / 2
+    amb = near_amb if exclude is None else (near_amb | exclude)
     err = np.abs(img.astype(np.float64) - ora["color"]).max(axis=0)
     bad = (err > IMAGE_ATOL) & ~amb
     assert not np.any(bad), (f"{bad.sum()} pixels exceed {IMAGE_ATOL}: max {err[bad].max():.3e} "
@@ -144,10 +143,31 @@ def compare_images(img: np.ndarray, final_T: np.ndarray, n_contrib: np.ndarray, 
         exact &= ~exclude
     nc_bad = (n_contrib.astype(np.int64) != ora["n_contrib"]) & exact
     assert not np.any(nc_bad), f"n_contrib differs on {nc_bad.sum()} pixels with no near decision"
-    frac = float(amb.mean())
+    frac = float(near_amb.mean())
     assert frac <= max_excluded_frac, f"{frac:.4f} of pixels excluded as ambiguous"
-    return dict(max_err=float(err[~amb].max(initial=0)), excluded=int(amb.sum()), near=int((~exact).sum()),
+    return dict(max_err=float(err[~amb].max(initial=0)), excluded=int(near_amb.sum()),
+                excluded_flip_tiles=int(0 if exclude is None else exclude.sum()), near=int((~exact).sum()),
                 pixels=int(err.size), n_contrib_mismatch=int(((n_contrib != ora["n_contrib"]) & ~exact).sum()))
+
+
+def flip_tile_mask(recs: np.ndarray, pre: dict, flipped: np.ndarray, cam, rows=(0, None)) -> np.ndarray:
+    """Pixels of the tiles in the symmetric difference of the GPU's and the
+    oracle's rectangle for each Gaussian whose rectangle flipped (each such
+    Gaussian must be flagged ambiguous; those tiles' lists legitimately
+    differ by that one Gaussian)."""
+    r0 = rows[0]
+    r1 = cam.height if rows[1] is None else rows[1]
+    mask = np.zeros((r1 - r0, cam.width), bool)
+    rg = rect_of(recs)
+    for g in flipped:
+        a = set((tx, ty) for ty in range(rg[g, 1], rg[g, 3]) for tx in range(rg[g, 0], rg[g, 2]))
+        x0, y0, x1, y1 = pre["rect"][g]
+        b = set((tx, ty) for ty in range(y0, y1) for tx in range(x0, x1))
+        for tx, ty in a ^ b:
+            ya, yb = max(ty * 16, r0), min(ty * 16 + 16, r1)
+            if ya < yb:
+                mask[ya - r0:yb - r0, tx * 16:tx * 16 + 16] = True
+    return mask
 
 
 def check_sorted_output(keys: np.ndarray, vals: np.ndarray, ranges: np.ndarray, m: int, recs: np.ndarray,

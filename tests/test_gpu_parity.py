@@ -11,7 +11,8 @@ import torch
 
 import paper_2509_25626_gb300 as gs
 from paper_2509_25626_gb300 import SPLAT_DTYPE, SceneTensors
-from parity import (check_sorted_output, compare_images, compare_preprocess, records_from_oracle, TAU_ALPHA, TAU_T)
+from parity import (ambiguous_gaussians, check_sorted_output, compare_images, compare_preprocess, flip_tile_mask,
+                    rect_of, records_from_oracle, TAU_ALPHA, TAU_T)
 from synth import clustered_scene, orbit_camera, pinhole_camera, tiny_scene, uniform_box_scene, Scene
 
 pytestmark = pytest.mark.gpu
@@ -126,16 +127,13 @@ def test_end_to_end_parity(case, oracle_frames):
         assert m == srt["m"] and np.array_equal(keys, srt["keys"]) and np.array_equal(vals_np, srt["vals"])
         assert np.array_equal(ranges_np, srt["ranges"])
     else:
+        assert np.all(ambiguous_gaussians(pre, cam)[flipped]), "a rectangle flipped on a non-ambiguous Gaussian"
+        assert len(flipped) <= max(2, sc.n // 1000)
         keep_g = ~np.isin(vals_np, flipped)
         keep_o = ~np.isin(srt["vals"], flipped)
         assert np.array_equal(keys[keep_g], srt["keys"][keep_o])
-        # tiles whose lists changed are excluded from the image comparison
-        tiles = np.unique((srt["keys"][~keep_o] >> np.uint64(32)).astype(np.int64))
-        tiles = np.union1d(tiles, (keys[~keep_g] >> np.uint64(32)).astype(np.int64))
-        exclude = np.zeros((cam.height, cam.width), bool)
-        for t in tiles:
-            ty, tx = divmod(int(t), cam.tiles_x)
-            exclude[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+        assert np.array_equal(vals_np[keep_g], srt["vals"][keep_o])
+        exclude = flip_tile_mask(recs, pre, flipped, cam)
     out, T, nc = gs.render(sp, vals, ranges, cam, bg=(0.1, 0.2, 0.3))
     torch.cuda.synchronize()
     rep = compare_images(out.cpu().numpy(), T.cpu().numpy(), nc.cpu().numpy(), img, exclude)
@@ -264,11 +262,9 @@ def test_full_size_scene_sampled(oracle):
     g_img = ws_probe.image.cpu().numpy()[:, sl]
     g_T = ws_probe.final_T.cpu().numpy()[sl]
     g_nc = ws_probe.n_contrib.cpu().numpy()[sl]
-    amb = np.zeros(g_T.shape, bool)
-    flips = np.nonzero(recs["tiles_touched"].astype(np.int64) != pre["tiles"])[0]
-    for g in flips:  # tiles of Gaussians whose rectangle flipped are excluded
-        x0, y0, x1, y1 = pre["rect"][g]
-        for ty in range(max(y0, rows[0] // 16), min(max(y1, y0 + 1), rows[1] // 16)):
-            amb[(ty * 16 - rows[0]):(ty * 16 - rows[0] + 16), :] = True
-    rep = compare_images(g_img, g_T, g_nc, band, exclude=amb, max_excluded_frac=0.02)
+    flips = np.nonzero((recs["tiles_touched"].astype(np.int64) != pre["tiles"]) |
+                       np.any(rect_of(recs) != pre["rect"], axis=1))[0]
+    assert np.all(ambiguous_gaussians(pre, cam)[flips]), "a rectangle flipped on a non-ambiguous Gaussian"
+    amb = flip_tile_mask(recs, pre, flips, cam, rows=rows)
+    rep = compare_images(g_img, g_T, g_nc, band, exclude=amb)
     print("full size", m, rep)

@@ -45,6 +45,7 @@ enum {
     GS_ERR_CAPACITY = -2,    /* more tile instances than the key buffers hold */
     GS_ERR_CUDA = -3,        /* a CUDA launch or runtime call failed */
     GS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    GS_ERR_TOO_LARGE = -5,   /* size beyond gs_sort_static's fixed scratch */
 };
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  Host memory. */
@@ -158,6 +159,29 @@ int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *rang
 int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
                        void *stream);
+
+/* gs_sort without a caller-provided workspace, for callers that cannot
+ * allocate device memory: code running inside another framework's memory
+ * pool, a plugin that is handed only its input and output buffers, or a
+ * service that reserves all device memory up front.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Same arguments, results and errors as gs_sort minus the workspace.  The
+ * scratch is a fixed 36 MiB array inside the library, which every GPU that
+ * loads the library holds until the process exits; it bounds the sizes:
+ * n <= GS_SORT_STATIC_MAX_GAUSSIANS and m_cap <= GS_SORT_STATIC_MAX_INSTANCES,
+ * else GS_ERR_TOO_LARGE (checked before any GPU work).  The call allocates
+ * nothing.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it:
+ * make that first call before any stream capture.  All calls share the
+ * array; each call clears the counters that must start at zero, but calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it, so serialise them.  With m_out NULL an overflow cannot be read back
+ * (the counters live in the shared array): pass m_out unless m_cap bounds M. */
+#define GS_SORT_STATIC_MAX_GAUSSIANS (1 << 19)
+#define GS_SORT_STATIC_MAX_INSTANCES (1 << 21)
+int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *keys, uint32_t *vals,
+                   int64_t m_cap, uint32_t *ranges, int64_t *m_out, void *stream);
 
 /* Text for a GS_* code, or the CUDA error string of the last GS_ERR_CUDA. */
 const char *gs_strerror(int code);

@@ -3,7 +3,7 @@ hot path: preprocess -> duplicate keys -> radix sort -> tile ranges ->
 per-tile alpha blending, behind the C ABI in include/gs.h (libgs.so).
 """
 
-from ._lib import GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_INVALID_ARG, GS_OK, SPLAT_DTYPE, GsError  # noqa: F401
+from ._lib import GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_INVALID_ARG, GS_ERR_TOO_LARGE, GS_OK, SPLAT_DTYPE, GsError  # noqa: F401
 from .api import (  # noqa: F401
     Renderer,
     SceneTensors,
@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     render,
     render_workload,
     sort,
+    sort_static,
     sort_status,
     sort_workspace_bytes,
 )

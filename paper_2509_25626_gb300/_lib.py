@@ -19,6 +19,9 @@ GS_ERR_INVALID_ARG = -1
 GS_ERR_CAPACITY = -2
 GS_ERR_CUDA = -3
 GS_ERR_TIMEOUT = -4
+GS_ERR_TOO_LARGE = -5
+SORT_STATIC_MAX_GAUSSIANS = 1 << 19
+SORT_STATIC_MAX_INSTANCES = 1 << 21
 
 c_float, c_int32, c_int64, c_void_p, c_size_t = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_size_t)
@@ -67,6 +70,9 @@ def lib():
                               ctypes.POINTER(c_int64), P]
         L.gs_sort_status.argtypes = [P, ctypes.POINTER(c_int64), P]
         L.gs_render.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P]
+        L.gs_sort_static.argtypes = [P, c_int64, ctypes.POINTER(GsCamera), P, P, c_int64, P,
+                                     ctypes.POINTER(c_int64), P]
+        L.gs_sort_static.restype = ctypes.c_int
         L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P]
         L.gs_strerror.argtypes = [ctypes.c_int]
         L.gs_strerror.restype = ctypes.c_char_p
@@ -91,4 +97,5 @@ def check(code: int, what: str) -> int:
 def exported_symbols():
     """Names of the gs_* functions the header declares."""
     return ["gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
-            "gs_render_workload", "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]
+            "gs_render_workload", "gs_sort_static", "gs_strerror", "gs_last_cuda_error", "gs_version",
+            "gs_built_arch"]

@@ -129,6 +129,29 @@ def sort(splats: torch.Tensor, n: int, cam, m_cap: int, keys=None, vals=None, ra
     return keys, vals, ranges, (int(m.value) if count else None), workspace
 
 
+def sort_static(splats: torch.Tensor, n: int, cam, m_cap: int, keys=None, vals=None, ranges=None,
+                count: bool = True, stream=None):
+    """gs_sort_static: gs_sort with the library's fixed scratch instead of a
+    workspace, for callers that cannot allocate device memory (the keys,
+    values and ranges outputs are still the caller's)."""
+    dev = splats.device
+    T = num_tiles(cam)
+    if keys is None:
+        keys = torch.empty(max(m_cap, 1), dtype=torch.int64, device=dev)
+    if vals is None:
+        vals = torch.empty(max(m_cap, 1), dtype=torch.int32, device=dev)
+    if ranges is None:
+        ranges = torch.empty((T, 2), dtype=torch.int32, device=dev)
+    for t, dt, nm in ((keys, torch.int64, "keys"), (vals, torch.int32, "vals"), (ranges, torch.int32, "ranges")):
+        _check_tensor(t, dt, nm)
+    c = camera_struct(cam)
+    m = ctypes.c_int64(-1)
+    code = L.lib().gs_sort_static(_ptr(splats), int(n), ctypes.byref(c), _ptr(keys), _ptr(vals), int(m_cap),
+                                  _ptr(ranges), ctypes.byref(m) if count else None, _stream(stream))
+    L.check(code, "gs_sort_static")
+    return keys, vals, ranges, (int(m.value) if count else None)
+
+
 def sort_status(workspace: torch.Tensor, stream=None):
     """(M, overflowed) of the last gs_sort on this workspace (synchronises)."""
     m = ctypes.c_int64(-1)

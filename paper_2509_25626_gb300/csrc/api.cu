@@ -149,6 +149,7 @@ const char *gs_strerror(int code) {
         case GS_ERR_CAPACITY: return "tile instances exceed the key buffer capacity";
         case GS_ERR_CUDA: return g_cuda_err;
         case GS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GS_ERR_TOO_LARGE: return "size exceeds the fixed scratch of gs_sort_static";
         default: return "unknown gs error code";
     }
 }

@@ -8,7 +8,7 @@
 // a caller-provided workspace.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads
-// the library holds it (35 MiB) until the process exits.  Host code cannot
+// the library holds it (36 MiB) until the process exits.  Host code cannot
 // use the array's name as a device address, so the first call on each
 // device resolves the address with cudaGetSymbolAddress (with that device
 // current) and caches it; make that first call before any stream capture.
@@ -57,7 +57,9 @@ extern "C" int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera
     if (!ranges || !aligned(ranges, 8)) return GS_ERR_INVALID_ARG;
     if (n > 0 && (!splats || !aligned(splats, 16))) return GS_ERR_INVALID_ARG;
     if (m_cap > 0 && (!keys || !vals || !aligned(keys, 16) || !aligned(vals, 16))) return GS_ERR_INVALID_ARG;
-    if (carve_sort_ws(nullptr, n, m_cap, nullptr) > kStaticScratchBytes) return GS_ERR_TOO_LARGE;
+    const uint64_t tiles_x = (uint64_t)((cam->width + kTile - 1) / kTile);
+    const uint64_t num_tiles = tiles_x * (uint64_t)((cam->height + kTile - 1) / kTile);
+    if (carve_sort_ws(nullptr, n, m_cap, num_tiles, nullptr) > kStaticScratchBytes) return GS_ERR_TOO_LARGE;
 
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -77,19 +79,18 @@ extern "C" int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera
         return GS_ERR_CUDA;
     }
 
-    const uint64_t tiles_x = (uint64_t)((cam->width + kTile - 1) / kTile);
-    const uint64_t num_tiles = tiles_x * (uint64_t)((cam->height + kTile - 1) / kTile);
     cudaStream_t st = (cudaStream_t)stream;
     SortWs ws;
-    carve_sort_ws(static_cast<char *>(slot.ptr), n, m_cap, &ws);
+    carve_sort_ws(static_cast<char *>(slot.ptr), n, m_cap, num_tiles, &ws);
     e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, st);
     if (e == cudaSuccess && m_out) {
-        uint64_t m = 0;
-        e = cudaMemcpyAsync(&m, &ws.hdr->m_total, sizeof(m), cudaMemcpyDeviceToHost, st);
+        SortHeader h;
+        e = cudaMemcpyAsync(&h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) {
-            *m_out = (int64_t)m;
-            if (m > (uint64_t)m_cap) return GS_ERR_CAPACITY;
+            *m_out = (int64_t)h.m_total;
+            if (h.timeout) return GS_ERR_TIMEOUT;
+            if (h.m_total > (uint64_t)m_cap) return GS_ERR_CAPACITY;
         }
     }
     if (e == cudaSuccess)

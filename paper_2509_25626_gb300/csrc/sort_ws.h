@@ -6,32 +6,52 @@
 
 namespace gs {
 
+constexpr int kSortTileItems = 4096;   // elements per block in the look-back scans and radix passes
+constexpr int kMaxTilePasses = 4;      // 8-bit digits of a 32-bit tile id
+constexpr int kDupItems = 2048;        // instances per duplicate block
+
 // Device-side counters of one gs_sort call (first 256 bytes of the workspace).
 struct SortHeader {
-    uint64_t m_total;   // instances the visible splats produce (may exceed the capacity)
-    uint32_t nvis;      // visible splats (tiles_touched > 0)
-    uint32_t m_sort;    // min(m_total, m_cap): instances actually written and sorted
-    uint32_t overflow;  // 1 if m_total > m_cap
-    uint32_t reserved[3];
+    uint64_t m_total;      // instances the visible splats produce (may exceed the capacity)
+    uint32_t nvis;         // visible splats (tiles_touched > 0)
+    uint32_t m_sort;       // min(m_total, m_cap): instances actually written and sorted
+    uint32_t overflow;     // 1 if m_total > m_cap
+    uint32_t timeout;      // 1 if a bounded look-back wait gave up (results invalid)
+    uint32_t tile_ctr[10]; // dynamic block-id counters, one per look-back kernel
+    uint32_t reserved[48];
 };
+static_assert(sizeof(SortHeader) == 256, "header is 256 bytes");
 
 struct SortWs {
     SortHeader *hdr;
-    uint32_t *dkey[2], *dval[2];   // depth sort ping-pong, [n]
-    uint32_t *tcount;              // tiles_touched in depth order, [n]
-    uint32_t *blk;                 // per-block sums, [scan blocks]
-    uint64_t *blk_off;             // their exclusive scan, [scan blocks]
-    uint64_t *key_alt;             // tile sort ping-pong, [m_cap]
-    uint32_t *val_alt;             // [m_cap]
-    uint32_t *hist;                // radix histograms, [256][radix tiles]
-    uint32_t *dtotal;              // radix digit totals, [256]
+    uint64_t *scan_state[2];            // look-back flags of the two scans, [blocks(n)]
+    uint64_t *depth_state[4];           // per pass, [blocks(n)][256]
+    uint64_t *tile_state[kMaxTilePasses];  // per pass, [blocks(m_cap)][256]
+    uint32_t *hist_depth;               // [4][256] digit totals
+    uint32_t *hist_tile;                // [kMaxTilePasses][256]
+    size_t zero_bytes;                  // bytes from hdr that must be zero at the start of a call
+    uint32_t *dkey[2], *dval[2];        // depth sort ping-pong, [n]
+    uint32_t *depthv;                   // FP32 depth bits by Gaussian id, [n]
+    uint32_t *offs;                     // first instance of each depth-sorted splat, [n]
+    uint32_t *dup_start;                // depth-sorted splat holding each duplicate block's first instance
+    uint32_t *tkey, *tval;              // tile sort buffer, [m_cap] each
 };
 
-uint32_t radix_tiles_for(uint64_t count);
-uint32_t scan_blocks_for(uint64_t count);
+inline uint64_t sort_blocks_for(uint64_t count) { return (count + kSortTileItems - 1) / kSortTileItems; }
+
+inline int tile_bits_of(uint64_t num_tiles) {
+    int b = 0;
+    while (b < 32 && (1ull << b) < num_tiles) ++b;
+    return b;
+}
+
+inline int tile_passes_of(uint64_t num_tiles) {
+    const int p = (tile_bits_of(num_tiles) + 7) / 8;
+    return p < 1 ? 1 : p;
+}
 
 // Carves `base` (may be null to only measure) and returns the bytes needed.
-inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, SortWs *ws) {
+inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, uint64_t num_tiles, SortWs *ws) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         char *p = base ? base + off : nullptr;
@@ -39,21 +59,26 @@ inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, SortWs *ws) {
         return p;
     };
     const uint64_t nn = (uint64_t)(n > 0 ? n : 0), mc = (uint64_t)(m_cap > 0 ? m_cap : 0);
-    const uint64_t nblk = scan_blocks_for(nn) + 1;
-    const uint64_t rt = radix_tiles_for(nn > mc ? nn : mc) + 1;
-    SortWs w;
-    w.hdr = reinterpret_cast<SortHeader *>(take(256));
+    const uint64_t bn = sort_blocks_for(nn) + 1, bm = sort_blocks_for(mc) + 1;
+    const int passes = tile_passes_of(num_tiles);
+    SortWs w{};
+    w.hdr = reinterpret_cast<SortHeader *>(take(sizeof(SortHeader)));
+    for (int i = 0; i < 2; ++i) w.scan_state[i] = reinterpret_cast<uint64_t *>(take(8 * bn));
+    for (int i = 0; i < 4; ++i) w.depth_state[i] = reinterpret_cast<uint64_t *>(take(8 * 256 * bn));
+    for (int i = 0; i < kMaxTilePasses; ++i)
+        w.tile_state[i] = reinterpret_cast<uint64_t *>(i < passes ? take(8 * 256 * bm) : nullptr);
+    w.hist_depth = reinterpret_cast<uint32_t *>(take(4 * 4 * 256));
+    w.hist_tile = reinterpret_cast<uint32_t *>(take(4 * kMaxTilePasses * 256));
+    w.zero_bytes = off;
     for (int i = 0; i < 2; ++i) {
         w.dkey[i] = reinterpret_cast<uint32_t *>(take(4 * nn));
         w.dval[i] = reinterpret_cast<uint32_t *>(take(4 * nn));
     }
-    w.tcount = reinterpret_cast<uint32_t *>(take(4 * nn));
-    w.blk = reinterpret_cast<uint32_t *>(take(4 * nblk));
-    w.blk_off = reinterpret_cast<uint64_t *>(take(8 * nblk));
-    w.key_alt = reinterpret_cast<uint64_t *>(take(8 * mc));
-    w.val_alt = reinterpret_cast<uint32_t *>(take(4 * mc));
-    w.hist = reinterpret_cast<uint32_t *>(take(4 * 256 * rt));
-    w.dtotal = reinterpret_cast<uint32_t *>(take(4 * 256));
+    w.depthv = reinterpret_cast<uint32_t *>(take(4 * nn));
+    w.offs = reinterpret_cast<uint32_t *>(take(4 * nn));
+    w.dup_start = reinterpret_cast<uint32_t *>(take(4 * ((mc + kDupItems - 1) / kDupItems + 2)));
+    w.tkey = reinterpret_cast<uint32_t *>(take(4 * mc));
+    w.tval = reinterpret_cast<uint32_t *>(take(4 * mc));
     if (ws) *ws = w;
     return off;
 }

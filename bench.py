@@ -40,6 +40,7 @@ def parse_args():
     p.add_argument("--workload", default="fwd_3m_1600x1064")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-backward", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
     return p.parse_args()
 
@@ -232,7 +233,7 @@ def main():
     vis = []
     for cam in cams[:1]:
         gs.preprocess(st, cam, r.splats)
-        vis.append(int((r.splats.view(torch.int32)[:, 11] > 0).sum().item()))
+        vis.append(int((r.splats.view(torch.int32)[:, 12] > 0).sum().item()))  # tiles_touched
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: (k * world + rank) % P
@@ -342,6 +343,10 @@ def main():
     tb = max(0, math.ceil(math.log2(T))) if T > 1 else 0
     launches_per_frame = 1 + 17 + 2 + 3 * ((tb + 7) // 8) + 1
 
+    backward = None
+    if not args.no_backward:
+        backward = measure_backward(gs, dev, steps=max(3, min(args.steps // 20, 50)), warmup=3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_frame_sample(scene, cams[used[0]], rows_tiles=args.cpu_rows)
@@ -359,7 +364,7 @@ def main():
                         instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
                         m_cap=m_cap, parallelism=f"replicas{world}",
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
-            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
+            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,
             peaks_src=peaks["src"],
         )
@@ -367,6 +372,36 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_backward(gs, dev, steps: int, warmup: int):
+    """Forward + backward of the 1M-Gaussian 1237x822 workload (orbit poses,
+    upstream gradient N(0, 1) per pixel and channel): ms per training step."""
+    import numpy as np
+    import torch
+    from synth import CONFIGS
+    wl = CONFIGS["bwd_1m_1237x822"]
+    scene = wl["scene"]()
+    cams = wl["cameras"]()
+    params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev).requires_grad_(True) for a in scene.arrays()]
+    g = torch.Generator(device=dev).manual_seed(0)
+    dL = torch.randn((3, cams[0].height, cams[0].width), generator=g, device=dev)
+    def step(k):
+        img = gs.rasterize(*params, cams[k % len(cams)], (0.0, 0.0, 0.0), 3)
+        img.backward(dL)
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for k in range(steps):
+        step(k)
+    e.record()
+    torch.cuda.synchronize(dev)
+    ms = s.elapsed_time(e) / steps
+    return dict(workload="bwd_1m_1237x822", gaussians=scene.n, width=cams[0].width, height=cams[0].height,
+                steps=steps, ms_per_step=ms, steps_per_s=1000.0 / ms,
+                note="forward + backward through gs.rasterize (one host sync per forward for the sort's M)")
 
 
 def kernel_sha(name: str) -> str:

@@ -78,19 +78,22 @@ typedef struct gs_scene {
  *     -0.5 d^T Sigma'^-1 d * log2(e) = -(u*u + v*v),
  *     u = w00 dx + w01 dy,   v = w11 dy,
  * and alpha = min(0.99, 2^(log2_opacity - u*u - v*v)).
- * A culled Gaussian has radius = 0 and tiles_touched = 0. */
+ * cull_hx / cull_hy bound the region where alpha can reach 1/255: outside
+ * |dx| <= cull_hx, |dy| <= cull_hy the splat is skipped for every pixel (the
+ * bound is the ellipse's bounding box, widened by 2^-10 relative + 1/64
+ * pixel to absorb FP32 rounding); both are negative if alpha < 1/255
+ * everywhere.  A culled Gaussian has radius = 0 and tiles_touched = 0. */
 typedef struct gs_splat {
     float x, y;               /* pixel-space mean */
     float w00, w01, w11;      /* inverse-covariance factor (see above) */
     float log2_opacity;       /* log2(sigmoid(logit)) */
     float r, g, b;            /* SH colour + 0.5, clamped at 0 */
+    float cull_hx, cull_hy;   /* half-extents of the alpha >= 1/255 region */
     float depth;              /* view-space z, FP32; its bits form the sort key */
-    int32_t radius;           /* ceil(3 sqrt(lambda_max(Sigma'))) pixels */
     uint32_t tiles_touched;   /* (x1 - x0) (y1 - y0) */
     uint32_t rect_lo;         /* x0 | y0 << 16, tile rectangle, inclusive */
     uint32_t rect_hi;         /* x1 | y1 << 16, exclusive */
-    float opacity;            /* sigmoid(logit) */
-    float reserved;
+    int32_t radius;           /* ceil(3 sqrt(lambda_max(Sigma'))) pixels */
 } gs_splat;
 
 /* Section II-B (1), projection step.  One thread per Gaussian:
@@ -106,8 +109,9 @@ typedef struct gs_splat {
 int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, void *stream);
 
 /* Bytes of device workspace gs_sort needs for n Gaussians, m_cap tile
- * instances and num_tiles = ceil(W/16) * ceil(H/16) tiles (>= 256-byte
- * aligned by the caller). */
+ * instances and num_tiles = ceil(W/16) * ceil(H/16) tiles (the workspace
+ * must be 256-byte aligned).  gs_sort also uses the key buffer (8 bytes per
+ * instance) as scratch until its last pass. */
 size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles);
 
 /* Section II-B: replicate every visible splat for each tile of its
@@ -123,7 +127,7 @@ size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles);
  * workspace: device, gs_sort_workspace_bytes(n, m_cap, num_tiles) bytes.
  * m_out: HOST pointer or NULL.  If non-NULL the call synchronises the stream
  * once to read M, stores it, and returns GS_ERR_CAPACITY (having written
- * nothing else) when M > m_cap.  If NULL the call never synchronises: M
+ * nothing else) when M > m_cap, GS_ERR_TIMEOUT if a bounded wait gave up.  If NULL the call never synchronises: M
  * stays on the device, an overflow is recorded there, only the first m_cap
  * instances are sorted, and gs_sort_status() reports it later.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
@@ -133,7 +137,9 @@ int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *k
 
 /* Read back the device-side instance count and overflow flag of the last
  * gs_sort that used `workspace` (synchronises `stream`).  m_out: host, the
- * true M (which may exceed m_cap).  Returns GS_OK or GS_ERR_CAPACITY. */
+ * true M (which may exceed m_cap).  Returns GS_OK, GS_ERR_CAPACITY, or
+ * GS_ERR_TIMEOUT if one of the sort's bounded inter-block waits gave up
+ * (the output is then invalid; it does not happen when blocks progress). */
 int gs_sort_status(const void *workspace, int64_t *m_out, void *stream);
 
 /* Section II-B (2), Algorithm 1, Eq. 1: one 16x16 thread block per tile walks
@@ -148,6 +154,37 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream);
  * 4-byte elements.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
               const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream);
+
+/* Gradients of a loss with respect to the scene parameters (device, each
+ * [n]-major like gs_scene, written -- not accumulated -- by the call). */
+typedef struct gs_scene_grads {
+    float *dmeans;          /* [n][3] */
+    float *dlog_scales;     /* [n][3] */
+    float *dquats;          /* [n][4] */
+    float *dopacity_logits; /* [n] */
+    float *dsh;             /* [n][16][3]; bands above sh_degree get 0 */
+} gs_scene_grads;
+
+/* Bytes of device workspace gs_render_backward needs for n Gaussians.  On
+ * return the workspace holds, per Gaussian, the gradient with respect to its
+ * 2D splat: float [n][12] = dL/d(x, y, conic a, b, c, opacity, r, g, b)
+ * and 3 unused floats (power = -(a dx^2 + c dy^2)/2 - b dx dy). */
+size_t gs_backward_workspace_bytes(int64_t n);
+
+/* Backward of gs_preprocess + gs_render for the same scene, camera and
+ * background, given dL_dcolor [3][H][W] (device): Eq. 1 differentiated per
+ * pixel back to front from n_contrib, the transmittance in front of each
+ * blended splat recovered from final_T as T_after / (1 - alpha) (no
+ * per-splat state is kept by the forward), then the chain rule through the
+ * preprocessing of Section II-B (1).  Piecewise: skipped splats, the 0.99
+ * clamp and clamped colour channels pass no gradient; the tile lists and the
+ * sort are constant.  splats, vals, ranges, final_T, n_contrib: the forward's
+ * outputs.  workspace: gs_backward_workspace_bytes(n) bytes, 16-byte aligned.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_render_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const uint32_t *vals,
+                       const uint32_t *ranges, const float bg[3], const float *final_T, const uint32_t *n_contrib,
+                       const float *dL_dcolor, void *workspace, size_t workspace_bytes,
+                       const gs_scene_grads *grads, void *stream);
 
 /* gs_render plus, per pixel, the number of splats evaluated before the
  * pixel stopped (the stopping splat included; all of the tile's splats if it
@@ -182,6 +219,41 @@ int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint3
 #define GS_SORT_STATIC_MAX_INSTANCES (1 << 21)
 int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *keys, uint32_t *vals,
                    int64_t m_cap, uint32_t *ranges, int64_t *m_out, void *stream);
+
+/* One request of a batched render: the inputs and outputs of a gs_render
+ * call (all device pointers) plus its first work item.  72 bytes. */
+typedef struct gs_render_job {
+    const gs_splat *splats;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    float *out_color;       /* [3][height][width] */
+    float *final_T;         /* [height][width] */
+    uint32_t *n_contrib;    /* [height][width] */
+    int32_t width, height;
+    float bg[3];
+    uint32_t tile_begin;    /* sum of the tile counts of the jobs before it */
+} gs_render_job;
+
+/* A batch, in device memory: jobs[0 .. n_jobs) sorted by tile_begin, and
+ * total_tiles = the sum of all their tile counts. */
+typedef struct gs_render_batch_desc {
+    int32_t n_jobs;
+    uint32_t total_tiles;
+    uint64_t reserved;
+    gs_render_job jobs[1];  /* n_jobs entries follow */
+} gs_render_batch_desc;
+
+/* gs_render for many requests in one persistent launch: blocks take (job,
+ * tile) work items from `counter` (device uint32, reset by the call) and run
+ * exactly gs_render's per-tile blend on each, so every job's outputs equal a
+ * gs_render call with the same inputs, bit for bit.  The batch is read from
+ * device memory, so the call (a memset and one kernel) can be captured once
+ * in a CUDA graph and replayed for any batch after rewriting `desc`.
+ * grid: blocks to launch, 0 = one full wave of the device (looked up on the
+ * first such call per device; make that call before any stream capture).
+ * The caller must keep jobs' buffers alive until the launch completes.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t grid, void *stream);
 
 /* Text for a GS_* code, or the CUDA error string of the last GS_ERR_CUDA. */
 const char *gs_strerror(int code);

@@ -40,10 +40,15 @@ class GsScene(ctypes.Structure):
 # numpy view of one gs_splat record (64 bytes)
 SPLAT_DTYPE = np.dtype([
     ("x", "<f4"), ("y", "<f4"), ("w00", "<f4"), ("w01", "<f4"), ("w11", "<f4"), ("log2_opacity", "<f4"),
-    ("r", "<f4"), ("g", "<f4"), ("b", "<f4"), ("depth", "<f4"), ("radius", "<i4"), ("tiles_touched", "<u4"),
-    ("rect_lo", "<u4"), ("rect_hi", "<u4"), ("opacity", "<f4"), ("reserved", "<f4"),
+    ("r", "<f4"), ("g", "<f4"), ("b", "<f4"), ("cull_hx", "<f4"), ("cull_hy", "<f4"), ("depth", "<f4"),
+    ("tiles_touched", "<u4"), ("rect_lo", "<u4"), ("rect_hi", "<u4"), ("radius", "<i4"),
 ])
 assert SPLAT_DTYPE.itemsize == 64
+
+
+class GsSceneGrads(ctypes.Structure):
+    _fields_ = [("dmeans", c_void_p), ("dlog_scales", c_void_p), ("dquats", c_void_p),
+                ("dopacity_logits", c_void_p), ("dsh", c_void_p)]
 
 
 class GsError(RuntimeError):
@@ -73,7 +78,15 @@ def lib():
         L.gs_sort_static.argtypes = [P, c_int64, ctypes.POINTER(GsCamera), P, P, c_int64, P,
                                      ctypes.POINTER(c_int64), P]
         L.gs_sort_static.restype = ctypes.c_int
+        L.gs_render_batch.argtypes = [P, P, ctypes.c_int32, P]
+        L.gs_render_batch.restype = ctypes.c_int
         L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P]
+        L.gs_backward_workspace_bytes.argtypes = [c_int64]
+        L.gs_backward_workspace_bytes.restype = c_size_t
+        L.gs_render_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P, P,
+                                         ctypes.POINTER(c_float), P, P, P, P, c_size_t,
+                                         ctypes.POINTER(GsSceneGrads), P]
+        L.gs_render_backward.restype = ctypes.c_int
         L.gs_strerror.argtypes = [ctypes.c_int]
         L.gs_strerror.restype = ctypes.c_char_p
         L.gs_last_cuda_error.restype = ctypes.c_char_p
@@ -97,5 +110,6 @@ def check(code: int, what: str) -> int:
 def exported_symbols():
     """Names of the gs_* functions the header declares."""
     return ["gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
-            "gs_render_workload", "gs_sort_static", "gs_strerror", "gs_last_cuda_error", "gs_version",
-            "gs_built_arch"]
+            "gs_render_workload", "gs_sort_static", "gs_backward_workspace_bytes", "gs_render_backward",
+            "gs_render_batch",
+            "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

@@ -125,6 +125,10 @@ def sort(splats: torch.Tensor, n: int, cam, m_cap: int, keys=None, vals=None, ra
     m = ctypes.c_int64(-1)
     code = L.lib().gs_sort(_ptr(splats), int(n), ctypes.byref(c), _ptr(keys), _ptr(vals), int(m_cap), _ptr(ranges),
                            _ptr(workspace), workspace.numel(), ctypes.byref(m) if count else None, _stream(stream))
+    if code == L.GS_ERR_CAPACITY:
+        err = L.GsError(code, "gs_sort")
+        err.m = int(m.value)
+        raise err
     L.check(code, "gs_sort")
     return keys, vals, ranges, (int(m.value) if count else None), workspace
 
@@ -231,3 +235,69 @@ class Renderer:
 
     def instances(self, stream=None):
         return sort_status(self.workspace, stream)
+
+
+def render_backward(scene: SceneTensors, cam, splats, vals, ranges, final_T, n_contrib, dL_dcolor,
+                    bg=(0.0, 0.0, 0.0), workspace=None, stream=None):
+    """gs_render_backward: gradients of sum(dL_dcolor * image) with respect to
+    the scene tensors, as a dict; also the per-splat 2D gradients [n, 12]."""
+    dev = splats.device
+    n = scene.n
+    grads = {k: torch.empty_like(getattr(scene, k)) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                                  "sh")}
+    need = int(L.lib().gs_backward_workspace_bytes(n))
+    if workspace is None:
+        workspace = torch.empty(need // 4, dtype=torch.float32, device=dev)
+    dL = dL_dcolor.contiguous().to(torch.float32)
+    _check_tensor(dL, torch.float32, "dL_dcolor")
+    g = L.GsSceneGrads()
+    g.dmeans, g.dlog_scales, g.dquats = grads["means"].data_ptr(), grads["log_scales"].data_ptr(), \
+        grads["quats"].data_ptr()
+    g.dopacity_logits, g.dsh = grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr()
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    code = L.lib().gs_render_backward(ctypes.byref(scene.struct()), ctypes.byref(c), _ptr(splats), _ptr(vals),
+                                      _ptr(ranges), bgc, _ptr(final_T), _ptr(n_contrib), _ptr(dL), _ptr(workspace),
+                                      workspace.numel() * 4, ctypes.byref(g), _stream(stream))
+    L.check(code, "gs_render_backward")
+    return grads, workspace.view(-1, 12)[:max(n, 1)]
+
+
+class RasterizeGaussians(torch.autograd.Function):
+    """image = render(preprocess(scene), sort) with the CUDA backward.
+
+    forward(means, log_scales, quats, opacity_logits, sh, cam, bg, sh_degree)
+    -> image [3, H, W].  The sort's instance count is read once per call (one
+    host synchronisation) to size the key buffers."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, cam, bg=(0.0, 0.0, 0.0), sh_degree=3):
+        scene = SceneTensors(means.detach().contiguous(), log_scales.detach().contiguous(),
+                             quats.detach().contiguous(), opacity_logits.detach().contiguous(),
+                             sh.detach().contiguous(), int(sh_degree))
+        splats = preprocess(scene, cam)
+        cap = max(1024, 8 * scene.n)
+        try:
+            keys, vals, ranges, m, _ = sort(splats, scene.n, cam, cap)
+        except L.GsError as e:
+            if e.code != L.GS_ERR_CAPACITY:
+                raise
+            keys, vals, ranges, m, _ = sort(splats, scene.n, cam, e.m)
+        img, final_T, n_contrib = render(splats, vals, ranges, cam, bg)
+        ctx.save_for_backward(scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh, splats,
+                              vals, ranges, final_T, n_contrib)
+        ctx.cam, ctx.bg, ctx.sh_degree = cam, tuple(bg), int(sh_degree)
+        return img
+
+    @staticmethod
+    def backward(ctx, dL_dimg):
+        means, log_scales, quats, logits, sh, splats, vals, ranges, final_T, n_contrib = ctx.saved_tensors
+        scene = SceneTensors(means, log_scales, quats, logits, sh, ctx.sh_degree)
+        grads, _ = render_backward(scene, ctx.cam, splats, vals, ranges, final_T, n_contrib, dL_dimg, ctx.bg)
+        return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"], None,
+                None, None)
+
+
+def rasterize(means, log_scales, quats, opacity_logits, sh, cam, bg=(0.0, 0.0, 0.0), sh_degree=3):
+    """Differentiable render of a scene (see RasterizeGaussians)."""
+    return RasterizeGaussians.apply(means, log_scales, quats, opacity_logits, sh, cam, bg, sh_degree)

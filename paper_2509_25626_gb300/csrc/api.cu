@@ -16,6 +16,11 @@ cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat 
 cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, cudaStream_t st);
 cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
                              uint32_t num_tiles, uint64_t *keys, uint32_t *vals, uint32_t *ranges, cudaStream_t st);
+cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
+                                   const uint32_t *vals, const uint32_t *ranges, const float bg[3],
+                                   const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
+                                   float *dsplat, const gs_scene_grads &g, cudaStream_t st);
+cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
                           uint32_t *n_eval, cudaStream_t stream);
@@ -72,8 +77,7 @@ int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats,
 }
 
 size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles) {
-    (void)num_tiles;
-    return carve_sort_ws(nullptr, n, m_cap, nullptr);
+    return carve_sort_ws(nullptr, n, m_cap, (uint64_t)(num_tiles > 0 ? num_tiles : 1), nullptr);
 }
 
 int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *keys, uint32_t *vals, int64_t m_cap,
@@ -85,19 +89,20 @@ int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *k
     if (!ranges || !aligned(ranges, 8) || !workspace || !aligned(workspace, 256)) return GS_ERR_INVALID_ARG;
     if (n > 0 && (!splats || !aligned(splats, 16))) return GS_ERR_INVALID_ARG;
     if (m_cap > 0 && (!keys || !vals || !aligned(keys, 16) || !aligned(vals, 16))) return GS_ERR_INVALID_ARG;
-    if (workspace_bytes < gs_sort_workspace_bytes(n, m_cap, (int32_t)num_tiles)) return GS_ERR_INVALID_ARG;
+    if (workspace_bytes < carve_sort_ws(nullptr, n, m_cap, num_tiles, nullptr)) return GS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     SortWs ws;
-    carve_sort_ws(static_cast<char *>(workspace), n, m_cap, &ws);
+    carve_sort_ws(static_cast<char *>(workspace), n, m_cap, num_tiles, &ws);
     cudaError_t e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, st);
     if (e != cudaSuccess) return cuda_status(e);
     if (m_out) {
-        uint64_t m = 0;
-        e = cudaMemcpyAsync(&m, &ws.hdr->m_total, sizeof(m), cudaMemcpyDeviceToHost, st);
+        SortHeader h;
+        e = cudaMemcpyAsync(&h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(e);
-        *m_out = (int64_t)m;
-        if (m > (uint64_t)m_cap) return GS_ERR_CAPACITY;
+        *m_out = (int64_t)h.m_total;
+        if (h.timeout) return GS_ERR_TIMEOUT;
+        if (h.m_total > (uint64_t)m_cap) return GS_ERR_CAPACITY;
     }
     const int tiles_x = (cam->width + kTile - 1) / kTile;
     return cuda_status(launch_sort_back(splats, n, ws, (uint64_t)m_cap, tiles_x, (uint32_t)num_tiles, keys, vals,
@@ -112,6 +117,7 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     *m_out = (int64_t)h.m_total;
+    if (h.timeout) return GS_ERR_TIMEOUT;
     return h.overflow ? GS_ERR_CAPACITY : GS_OK;
 }
 
@@ -140,6 +146,41 @@ int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint3
                        void *stream) {
     if (!n_eval || !aligned(n_eval, 4)) return GS_ERR_INVALID_ARG;
     return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, n_eval, stream);
+}
+
+int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t grid, void *stream) {
+    if (!desc || !aligned(desc, 8) || !counter || !aligned(counter, 4) || grid < 0) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_batch(desc, counter, grid, (cudaStream_t)stream));
+}
+
+size_t gs_backward_workspace_bytes(int64_t n) { return (size_t)(n > 0 ? n : 1) * 12 * sizeof(float); }
+
+int gs_render_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const uint32_t *vals,
+                       const uint32_t *ranges, const float bg[3], const float *final_T, const uint32_t *n_contrib,
+                       const float *dL_dcolor, void *workspace, size_t workspace_bytes,
+                       const gs_scene_grads *grads, void *stream) {
+    if (!scene || !camera_ok(cam) || !grads || !bg) return GS_ERR_INVALID_ARG;
+    if (scene->n < 0 || scene->n > (int64_t)UINT32_MAX || scene->sh_degree < 0 || scene->sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
+    if (!ranges || !aligned(ranges, 8) || !final_T || !n_contrib || !dL_dcolor || !aligned(final_T, 4) ||
+        !aligned(n_contrib, 4) || !aligned(dL_dcolor, 4))
+        return GS_ERR_INVALID_ARG;
+    if (!workspace || !aligned(workspace, 16) || workspace_bytes < gs_backward_workspace_bytes(scene->n))
+        return GS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        const void *ptrs[] = {scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh,
+                              splats, grads->dmeans, grads->dlog_scales, grads->dquats, grads->dopacity_logits,
+                              grads->dsh};
+        for (const void *p : ptrs)
+            if (!p || !aligned(p, 4)) return GS_ERR_INVALID_ARG;
+        if (!aligned(scene->quats, 16) || !aligned(splats, 16) || !vals) return GS_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_backward(*scene, make_cam_params(*cam), splats, vals, ranges, bg, final_T,
+                                              n_contrib, dL_dcolor, static_cast<float *>(workspace), *grads,
+                                              (cudaStream_t)stream));
 }
 
 const char *gs_strerror(int code) {

@@ -41,6 +41,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-backward", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
     return p.parse_args()
 
@@ -343,6 +344,10 @@ def main():
     tb = max(0, math.ceil(math.log2(T))) if T > 1 else 0
     launches_per_frame = 1 + 17 + 2 + 3 * ((tb + 7) // 8) + 1
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = measure_serving(gs, dev)
+
     backward = None
     if not args.no_backward:
         backward = measure_backward(gs, dev, steps=max(3, min(args.steps // 20, 50)), warmup=3)
@@ -364,7 +369,7 @@ def main():
                         instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
                         m_cap=m_cap, parallelism=f"replicas{world}",
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
-            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, backward=backward,
+            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, serving=serving, backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,
             peaks_src=peaks["src"],
         )
@@ -372,6 +377,43 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_serving(gs, dev, rate: float = 200.0, duration: float = 2.5):
+    """Continuous-batching server on three resident scenes (0.5M, 2M, 5M
+    Gaussians, clustered like the 3M workload), Poisson arrivals at `rate`
+    per second, each request a random orbit pose at a resolution drawn from
+    {640x480, 1280x720, 1600x1064, 1920x1080}.  Reports latency percentiles
+    and throughput of the batched server and of one-request-at-a-time
+    rendering on the same stream, plus both at saturation (all requests
+    present at t = 0)."""
+    from paper_2509_25626_gb300 import serve as S
+    from synth import clustered_scene, orbit_camera
+    specs = (("s0.5m", 500_000, 41), ("s2m", 2_000_000, 42), ("s5m", 5_000_000, 43))
+    scenes = {name: gs.SceneTensors.from_scene(clustered_scene(n, seed=sd), dev) for name, n, sd in specs}
+    res = [(640, 480), (1280, 720), (1600, 1064), (1920, 1080)]
+    srv = S.Server(scenes, max_batch=16, mem_budget=48 << 30, device=dev)
+    for name in scenes:
+        for w, h in res:
+            srv.calibrate(name, w, h, [orbit_camera(k, 6, 4.0, w, h) for k in range(6)])
+    cam_fn = lambda u, w, h: orbit_camera(u * 20.0, 20, 4.0, w, h)
+    srv.serve(S.poisson_requests(rate, 0.3, list(scenes), res, cam_fn, seed=97), realtime=True)  # warm-up
+    srv.serve_sequential(S.poisson_requests(rate, 0.1, list(scenes), res, cam_fn, seed=96), realtime=True)
+    out = {}
+    for mode in ("batched", "sequential"):
+        reqs = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=99)
+        fn = srv.serve if mode == "batched" else srv.serve_sequential
+        done, wall = fn(reqs, realtime=True)
+        out[mode] = S.latency_stats(done, wall)
+        sat = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=100)
+        for r in sat:
+            r.arrival = 0.0
+        done, wall = fn(sat, realtime=False)
+        out[mode]["saturated_frames_per_s"] = len(done) / wall
+    out.update(workload="serve_3scenes_poisson200", rate_per_s=rate, duration_s=duration,
+               scenes={name: n for name, n, _ in specs}, resolutions=[f"{w}x{h}" for w, h in res],
+               batches=int(srv.stats["batches"]), overflow_or_timeout=int(srv.stats["overflow_or_timeout"]))
+    return out
 
 
 def measure_backward(gs, dev, steps: int, warmup: int):

@@ -1,98 +1,221 @@
 // Per-tile front-to-back alpha blending (Section II-B (2), Algorithm 1,
 // Eq. 1 with the kernel's alpha and the Appendix B per-pixel rules).
 //
-// One 256-thread block per 16x16 tile, one pixel per thread.  The tile's
-// splats are staged in shared memory in batches of 256 (each thread gathers
-// one record), then every thread walks the batch front to back.  Exits are
-// block-uniform (__syncthreads_and at the batch boundary), so no thread
-// leaves while others still reach a barrier, and a pixel that stopped stays
-// stopped across batches.
+// One 128-thread block per 16x16 tile.  Each warp owns an 8x8 pixel block
+// and each lane two horizontally adjacent pixels, which share every term
+// that depends only on the row (dy, v, the w01 dy product).  Per round the
+// block stages up to 256 of the tile's splats in shared memory (two gathers
+// per thread) and marks, per warp, the splats whose alpha >= 1/255 bounding
+// box (gs_splat.cull_hx/hy) meets that warp's 8x8 block; each warp then
+// walks only its marked splats, front to back.  A splat left out has alpha
+// < 1/255 at every pixel of the block, so the per-pixel result, n_contrib
+// (a list position) and the stopping point are unchanged.
+//
+// Exits are block-uniform (__syncthreads_and at the round boundary) and
+// warp-uniform inside a round, so no thread leaves while others still reach
+// a barrier, and a pixel that stopped stays stopped across rounds.
 #include "common.cuh"
 
 namespace gs {
 
 namespace {
 
-constexpr int kBatch = 256;
+constexpr int kThreads = 128;  // 4 warps, 2x2 blocks of 8x8 pixels
+constexpr int kBatch = 256;    // splats staged per round
+constexpr int kWarps = kThreads / 32;
 
 struct __align__(16) StagedA { float x, y, w00, w01; };
 struct __align__(16) StagedB { float w11, lg2o, r, g; };
 
+struct Pixel {
+    float T, c0, c1, c2;
+    uint32_t last;  // 1-based list position of the last blended splat
+    uint32_t stop;  // list position of the splat that stopped the pixel, 0 if none
+    bool done;
+};
+
+__device__ __forceinline__ void blend(Pixel &p, float alpha, float r, float g, float b, uint32_t idx) {
+    if (p.done || alpha < kAlphaMin) return;
+    const float Tn = p.T * (1.0f - alpha);
+    if (Tn < kTStop) {  // stop without blending this splat
+        p.done = true;
+        p.stop = idx;
+        return;
+    }
+    const float w = alpha * p.T;
+    p.c0 = fmaf(r, w, p.c0);
+    p.c1 = fmaf(g, w, p.c1);
+    p.c2 = fmaf(b, w, p.c2);
+    p.T = Tn;
+    p.last = idx;
+}
+
 // kCount: also write, per pixel, how many splats were evaluated before the
-// pixel stopped (the stopping one included) -- the work measure of the
-// paper's workload characterisation (Table III).
+// pixel stopped (the stopping one included; the whole list if it never
+// stopped) -- the work measure of the paper's workload characterisation
+// (Table III).  It follows from the stopping position, so the loop is the
+// same in both instantiations.
+struct RenderSmem {
+    StagedA a[kBatch];
+    StagedB b[kBatch];
+    float c[kBatch];
+    uint8_t mask[kBatch];
+    uint8_t list[kWarps][kBatch];
+};
+
+// Renders one tile with the whole block.  Every thread must call it; it
+// begins and ends with block-wide barriers, so the shared memory may be
+// reused for the next tile.
 template <bool kCount>
-__global__ void __launch_bounds__(kTilePixels) render_kernel(const gs_splat *__restrict__ splats,
-                                                             const uint32_t *__restrict__ vals,
-                                                             const uint2 *__restrict__ ranges, int width, int height,
-                                                             int tiles_x, float bg_r, float bg_g, float bg_b,
-                                                             float *__restrict__ out_color,
-                                                             float *__restrict__ final_T,
-                                                             uint32_t *__restrict__ n_contrib,
-                                                             uint32_t *__restrict__ n_eval) {
-    __shared__ StagedA s_a[kBatch];
-    __shared__ StagedB s_b[kBatch];
-    __shared__ float s_c[kBatch];
+__device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__restrict__ splats,
+                                            const uint32_t *__restrict__ vals, const uint2 range, int tile,
+                                            int width, int height, int tiles_x, float bg_r, float bg_g, float bg_b,
+                                            float *__restrict__ out_color, float *__restrict__ final_T,
+                                            uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_eval) {
+    StagedA *s_a = sm.a;
+    StagedB *s_b = sm.b;
+    float *s_c = sm.c;
+    uint8_t *s_mask = sm.mask;
+    uint8_t(*s_list)[kBatch] = sm.list;
 
-    const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x >> 4);
-    const bool inside = px < width && py < height;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const int bx0 = tx * kTile + (int)(warp & 1u) * 8, by0 = ty * kTile + (int)(warp >> 1) * 8;
+    const int px = bx0 + 2 * (int)(lane & 3u), py = by0 + (int)(lane >> 2);
     const float pxf = (float)px, pyf = (float)py;
+    const bool in0 = px < width && py < height, in1 = px + 1 < width && py < height;
+    Pixel p0{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in0};
+    Pixel p1{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in1};
 
-    const uint2 range = ranges[tile];
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0, evals = 0;
-    bool done = !inside;
+    // corners of the tile, for the per-warp culling masks
+    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
+    const unsigned lt = lanemask_lt();
 
     for (uint32_t base = range.x; base < range.y; base += kBatch) {
-        // every thread has finished the previous batch; stop if all pixels are done
-        if (__syncthreads_and(done)) break;
-        const uint32_t i = base + threadIdx.x;
-        if (i < range.y) {
-            const float4 *rec = reinterpret_cast<const float4 *>(splats + vals[i]);
-            const float4 a = rec[0], b = rec[1], c = rec[2];
-            s_a[threadIdx.x] = StagedA{a.x, a.y, a.z, a.w};
-            s_b[threadIdx.x] = StagedB{b.x, b.y, b.z, b.w};
-            s_c[threadIdx.x] = c.x;
+        // every thread has finished the previous round; stop if all pixels are done
+        if (__syncthreads_and(p0.done && p1.done)) break;
+#pragma unroll
+        for (int r = 0; r < kBatch / kThreads; ++r) {
+            const int k = (int)threadIdx.x + r * kThreads;
+            const uint32_t i = base + (uint32_t)k;
+            uint32_t m = 0;
+            if (i < range.y) {
+                const float4 *src = reinterpret_cast<const float4 *>(splats + vals[i]);
+                const float4 a = src[0], b = src[1], c = src[2];
+                s_a[k] = StagedA{a.x, a.y, a.z, a.w};
+                s_b[k] = StagedB{b.x, b.y, b.z, b.w};
+                s_c[k] = c.x;
+                // box [x - hx, x + hx] x [y - hy, y + hy] against the 8x8 blocks
+                const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
+                const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
+                const uint32_t mx1 = (xhi >= tx0 + 8.f) & (xlo <= tx0 + 15.f);
+                const uint32_t my0 = (yhi >= ty0) & (ylo <= ty0 + 7.f);
+                const uint32_t my1 = (yhi >= ty0 + 8.f) & (ylo <= ty0 + 15.f);
+                m = (mx0 & my0) | ((mx1 & my0) << 1) | ((mx0 & my1) << 2) | ((mx1 & my1) << 3);
+                if (!(c.y >= 0.f)) m = 0;  // alpha < 1/255 everywhere (empty box)
+            }
+            s_mask[k] = (uint8_t)m;
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, range.y - base);
-        if (!done) {
-            for (int j = 0; j < cnt; ++j) {
-                if (kCount) ++evals;
-                const StagedA sa = s_a[j];
-                const StagedB sb = s_b[j];
-                const float dx = sa.x - pxf, dy = sa.y - pyf;
-                const float u = fmaf(sa.w00, dx, sa.w01 * dy);
-                const float v = sb.w11 * dy;
-                const float arg = fmaf(-u, u, fmaf(-v, v, sb.lg2o));
-                const float alpha = fminf(kAlphaMax, ex2_approx(arg));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < kTStop) {
-                    done = true;
-                    break;
-                }
-                const float w = alpha * T;
-                C0 = fmaf(sb.r, w, C0);
-                C1 = fmaf(sb.g, w, C1);
-                C2 = fmaf(s_c[j], w, C2);
-                T = Tn;
-                last = base - range.x + j + 1;
+
+        // this warp's splats, in list order
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int c = 0; c < kBatch / 32; ++c) {
+            const uint32_t bit = (s_mask[c * 32 + lane] >> warp) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            if (bit) s_list[warp][cnt + __popc(bal & lt)] = (uint8_t)(c * 32 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+
+        const uint32_t pos0 = base - range.x + 1;  // list position of staged splat 0
+        for (uint32_t q = 0; q < cnt; ++q) {
+            if ((q & 7u) == 0u && __all_sync(0xffffffffu, p0.done && p1.done)) break;
+            const uint32_t j = s_list[warp][q];
+            const StagedA sa = s_a[j];
+            const StagedB sb = s_b[j];
+            const float dy = sa.y - pyf;
+            const float dx = sa.x - pxf;
+            const float t = sa.w01 * dy;
+            const float u0 = fmaf(sa.w00, dx, t);
+            const float u1 = u0 - sa.w00;  // dx - 1 for the right-hand pixel
+            const float v = sb.w11 * dy;
+            const float vv = fmaf(-v, v, sb.lg2o);
+            const float a0 = fminf(kAlphaMax, ex2_approx(fmaf(-u0, u0, vv)));
+            const float a1 = fminf(kAlphaMax, ex2_approx(fmaf(-u1, u1, vv)));
+            if (a0 >= kAlphaMin || a1 >= kAlphaMin) {
+                const float b = s_c[j];
+                blend(p0, a0, sb.r, sb.g, b, pos0 + j);
+                blend(p1, a1, sb.r, sb.g, b, pos0 + j);
             }
         }
     }
-    if (inside) {
+
+    const size_t plane = (size_t)width * height;
+    const uint32_t len = range.y - range.x;
+    if (in0) {
         const size_t pix = (size_t)py * width + px;
-        const size_t plane = (size_t)width * height;
-        out_color[pix] = fmaf(T, bg_r, C0);
-        out_color[plane + pix] = fmaf(T, bg_g, C1);
-        out_color[2 * plane + pix] = fmaf(T, bg_b, C2);
-        final_T[pix] = T;
-        n_contrib[pix] = last;
-        if (kCount) n_eval[pix] = evals;
+        out_color[pix] = fmaf(p0.T, bg_r, p0.c0);
+        out_color[plane + pix] = fmaf(p0.T, bg_g, p0.c1);
+        out_color[2 * plane + pix] = fmaf(p0.T, bg_b, p0.c2);
+        final_T[pix] = p0.T;
+        n_contrib[pix] = p0.last;
+        if (kCount) n_eval[pix] = p0.stop ? p0.stop : len;
+    }
+    if (in1) {
+        const size_t pix = (size_t)py * width + px + 1;
+        out_color[pix] = fmaf(p1.T, bg_r, p1.c0);
+        out_color[plane + pix] = fmaf(p1.T, bg_g, p1.c1);
+        out_color[2 * plane + pix] = fmaf(p1.T, bg_b, p1.c2);
+        final_T[pix] = p1.T;
+        n_contrib[pix] = p1.last;
+        if (kCount) n_eval[pix] = p1.stop ? p1.stop : len;
+    }
+    __syncthreads();  // shared memory free for the next tile
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads) render_kernel(const gs_splat *__restrict__ splats,
+                                                          const uint32_t *__restrict__ vals,
+                                                          const uint2 *__restrict__ ranges, int width, int height,
+                                                          int tiles_x, float bg_r, float bg_g, float bg_b,
+                                                          float *__restrict__ out_color,
+                                                          float *__restrict__ final_T,
+                                                          uint32_t *__restrict__ n_contrib,
+                                                          uint32_t *__restrict__ n_eval) {
+    __shared__ RenderSmem sm;
+    render_tile<kCount>(sm, splats, vals, ranges[blockIdx.x], blockIdx.x, width, height, tiles_x, bg_r, bg_g, bg_b,
+                        out_color, final_T, n_contrib, n_eval);
+}
+
+// Persistent render of many jobs (requests): blocks pull work items -- one
+// (job, tile) each, numbered through the jobs' tile_begin prefix -- from an
+// atomic counter until all are taken.  The job table and its counts live in
+// device memory, so one captured launch serves any batch.
+__global__ void __launch_bounds__(kThreads) render_batch_kernel(const gs_render_batch_desc *__restrict__ desc,
+                                                                uint32_t *__restrict__ counter) {
+    __shared__ RenderSmem sm;
+    __shared__ uint32_t s_w;
+    const int n_jobs = desc->n_jobs;
+    const uint32_t total = desc->total_tiles;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t w = s_w;
+        __syncthreads();
+        if (w >= total) break;
+        int lo = 0, hi = n_jobs;  // last job with tile_begin <= w
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (desc->jobs[mid].tile_begin <= w) lo = mid; else hi = mid;
+        }
+        const gs_render_job &job = desc->jobs[lo];
+        const int tiles_x = (job.width + kTile - 1) / kTile;
+        const int tile = (int)(w - job.tile_begin);
+        render_tile<false>(sm, job.splats, job.vals, reinterpret_cast<const uint2 *>(job.ranges)[tile], tile,
+                           job.width, job.height, tiles_x, job.bg[0], job.bg[1], job.bg[2], job.out_color,
+                           job.final_T, job.n_contrib, nullptr);
     }
 }
 
@@ -103,13 +226,36 @@ cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const ui
                           uint32_t *n_eval, cudaStream_t stream) {
     const int num_tiles = cam.tiles_x * cam.tiles_y;
     if (n_eval)
-        render_kernel<true><<<num_tiles, kTilePixels, 0, stream>>>(
+        render_kernel<true><<<num_tiles, kThreads, 0, stream>>>(
             splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, cam.tiles_x, bg[0], bg[1],
             bg[2], out_color, final_T, n_contrib, n_eval);
     else
-        render_kernel<false><<<num_tiles, kTilePixels, 0, stream>>>(
+        render_kernel<false><<<num_tiles, kThreads, 0, stream>>>(
             splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, cam.tiles_x, bg[0], bg[1],
             bg[2], out_color, final_T, n_contrib, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {
+        // one full wave; looked up on the first call per device (make that
+        // call outside stream capture) and cached
+        static int wave[64] = {0};
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (wave[dev] == 0) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel, kThreads, 0);
+            wave[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        }
+        grid = wave[dev];
+    }
+    render_batch_kernel<<<grid, kThreads, 0, stream>>>(desc, counter);
     return cudaGetLastError();
 }
 

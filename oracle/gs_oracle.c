@@ -356,7 +356,9 @@ void oracle_duplicate_sort(int64_t n, const int32_t *rect, const int32_t *tiles,
  * T and contributor index, it reports:
  *   n_eval        Gaussians evaluated before the pixel stopped (the
  *                 "Gaussian-pixel evaluations" work count)
- *   near_count    decisions whose log-space margin is under tau
+ *   near_count    decisions whose log-space margin is under tau, widened by
+ *                 the effect of a relative rounding pos_eps of the splat's
+ *                 pixel coordinates (FP32 stores them with |x| ulp ~ |x| 2^-24)
  *   flip_impact   the largest bound, over those near decisions, on how much
  *                 one flipped decision could move any colour channel
  * ------------------------------------------------------------------------- */
@@ -371,7 +373,7 @@ typedef struct {
 
 static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int64_t len, const double *xy,
                                const double *conic, const double *opacity, const double *rgb, const double *bg,
-                               double tau_alpha, double tau_T, double cmax) {
+                               double tau_alpha, double tau_T, double pos_eps, double cmax) {
     pixel_t out;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     int32_t contrib = 0, last = 0, near = 0;
@@ -386,13 +388,17 @@ static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int6
         if (power > 0.0) continue;
         double raw = opacity[g] * exp(power);
         double alpha = fmin(ALPHA_MAX, raw);
-        if (raw > 0.0 && fabs(log(raw) - log(ALPHA_MIN)) < tau_alpha) {
+        /* margin widened by how far a relative rounding pos_eps of the mean's
+         * coordinates moves log(alpha): |d power / d x_g| pos_eps (|x_g| + 1) */
+        double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
+        double pos_err = pos_eps * (gx * (fabs(xy[2 * g]) + 1.0) + gy * (fabs(xy[2 * g + 1]) + 1.0));
+        if (raw > 0.0 && fabs(log(raw) - log(ALPHA_MIN)) < tau_alpha + pos_err) {
             ++near;
             impact = fmax(impact, 2.0 * ALPHA_MIN * T * (cmax + bgmax));
         }
         if (alpha < ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(log(Tn) - log(T_MIN)) < tau_T) {
+        if (fabs(log(Tn) - log(T_MIN)) < tau_T + pos_err * alpha / (1.0 - alpha)) {
             ++near;
             impact = fmax(impact, T * (cmax + bgmax));
         }
@@ -431,7 +437,7 @@ static void store_pixel(const pixel_t *p, int64_t pix, int64_t npix, double *out
  * nthreads OpenMP threads if built with OpenMP. */
 void oracle_render(int width, int height, int row0, int row1, const uint32_t *ranges, const uint32_t *vals,
                    int64_t n, const double *xy, const double *conic, const double *opacity, const double *rgb,
-                   const double *bg, double tau_alpha, double tau_T, int nthreads, double *out_color,
+                   const double *bg, double tau_alpha, double tau_T, double pos_eps, int nthreads, double *out_color,
                    double *final_T, int32_t *n_contrib, int32_t *n_eval, int32_t *near_count,
                    double *flip_impact) {
     int tiles_x = (width + TILE - 1) / TILE;
@@ -446,7 +452,7 @@ void oracle_render(int width, int height, int row0, int row1, const uint32_t *ra
             int tile = (py / TILE) * tiles_x + px / TILE;
             uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
             pixel_t p = composite_pixel((double)px, (double)py, vals + s, (int64_t)e - (int64_t)s, xy, conic,
-                                        opacity, rgb, bg, tau_alpha, tau_T, cmax);
+                                        opacity, rgb, bg, tau_alpha, tau_T, pos_eps, cmax);
             store_pixel(&p, (int64_t)py * width + px, npix, out_color, final_T, n_contrib, n_eval, near_count,
                         flip_impact);
         }
@@ -489,7 +495,7 @@ void oracle_render_bruteforce(int width, int height, int64_t n, const int32_t *r
             }
             qsort(ids, (size_t)len, sizeof(uint32_t), bf_cmp);
             pixel_t p = composite_pixel((double)px, (double)py, ids, len, xy, conic, opacity, rgb, bg, 0.0, 0.0,
-                                        cmax);
+                                        0.0, cmax);
             store_pixel(&p, (int64_t)py * width + px, npix, out_color, final_T, n_contrib, n_eval, near_count,
                         flip_impact);
         }

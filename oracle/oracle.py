@@ -56,7 +56,7 @@ def _load():
             lib.oracle_duplicate_sort.restype = None
             lib.oracle_duplicate_sort.argtypes = [i64, P, P, P, i32, i32, i64, P, P, P]
             lib.oracle_render.restype = None
-            lib.oracle_render.argtypes = [i32, i32, i32, i32, P, P, i64, P, P, P, P, P, f64, f64, i32] + [P] * 6
+            lib.oracle_render.argtypes = [i32, i32, i32, i32, P, P, i64, P, P, P, P, P, f64, f64, f64, i32] + [P] * 6
             lib.oracle_render_bruteforce.restype = None
             lib.oracle_render_bruteforce.argtypes = [i32, i32, i64, P, P, P, P, P, P, P, P, i32] + [P] * 6
             lib.oracle_sh_basis.restype = f64
@@ -171,10 +171,12 @@ def _render_outputs(w: int, h: int) -> dict:
 
 
 def render(pre: dict, srt: dict, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0, tau_T: float = 0.0,
-           rows: tuple | None = None, threads: int = 0) -> dict:
+           rows: tuple | None = None, threads: int = 0, pos_eps: float = 0.0) -> dict:
     """Tiled front-to-back compositing of every pixel in ``rows`` (default:
     all).  ``tau_alpha`` / ``tau_T`` set the log-space margin under which a
-    threshold decision counts as near (see ``near`` / ``flip_impact``)."""
+    threshold decision counts as near (see ``near`` / ``flip_impact``);
+    ``pos_eps`` widens it by the effect of that relative rounding of each
+    splat's pixel coordinates."""
     lib = _load()
     w, h = cam.width, cam.height
     r0, r1 = (0, h) if rows is None else rows
@@ -184,7 +186,7 @@ def render(pre: dict, srt: dict, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0
     n = pre["xy"].shape[0]
     lib.oracle_render(w, h, r0, r1, _p(np.ascontiguousarray(srt["ranges"])), _p(vals), n, _p(pre["xy"]),
                       _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(bgv), tau_alpha, tau_T,
-                      int(threads), *[_p(out[k]) for k in ("color", "final_T", "n_contrib", "n_eval", "near",
+                      float(pos_eps), int(threads), *[_p(out[k]) for k in ("color", "final_T", "n_contrib", "n_eval", "near",
                                                             "flip_impact")])
     return out
 
@@ -203,9 +205,10 @@ def render_bruteforce(pre: dict, cam, bg=(0.0, 0.0, 0.0), use_rect: bool = True)
     return out
 
 
-def frame(scene, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0, tau_T: float = 0.0, threads: int = 0):
+def frame(scene, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0, tau_T: float = 0.0, threads: int = 0,
+          pos_eps: float = 0.0):
     """Whole forward pass: preprocess, duplicate + sort + ranges, render."""
     pre = preprocess(scene, cam)
     srt = duplicate_sort(pre, cam)
-    img = render(pre, srt, cam, bg, tau_alpha, tau_T, threads=threads)
+    img = render(pre, srt, cam, bg, tau_alpha, tau_T, threads=threads, pos_eps=pos_eps)
     return pre, srt, img

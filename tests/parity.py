@@ -10,10 +10,14 @@ TAU_ALPHA, TAU_T
     A pixel is excluded from the 2e-4 check only if such a near decision
     could move it by more than IMAGE_ATOL / 2 (the oracle's flip_impact), and
     excluded from the exact n_contrib check if it has any near decision.
-    The FP32 error of the exponent is about 1e-6 (ex2.approx relative error
-    2^-22, position and conic rounding); TAU_ALPHA = 1e-4 leaves a factor of
-    ~100.  Transmittance accumulates one rounding per blend (<= ~2000 blends
-    before T < 1e-4), so TAU_T = 1e-3.
+    The FP32 error of the exponent from its own arithmetic is about 1e-6
+    (ex2.approx relative error 2^-22, conic rounding); TAU_ALPHA = 1e-4
+    leaves a factor of ~100.  Transmittance accumulates one rounding per
+    blend (<= ~2000 blends before T < 1e-4), so TAU_T = 1e-3.  On top, a
+    splat's FP32 pixel coordinates carry a rounding that grows with |x|; the
+    oracle widens each margin by |d power / d x| POS_EPS (|x| + 1), with
+    POS_EPS = 2^-23 (two ulps) when the GPU renders the oracle's own
+    coordinates rounded to FP32 and 2^-21 when it projects them itself.
 EDGE_TOL_PX, RADIUS_TOL
     Integer decisions of the preprocess (radius, tile rectangle) may flip
     only for Gaussians whose FP64 value lies this close to the boundary.
@@ -28,6 +32,8 @@ import numpy as np
 IMAGE_ATOL = 2e-4
 TAU_ALPHA = 1e-4
 TAU_T = 1e-3
+POS_EPS_RENDER = 2.0 ** -23
+POS_EPS_E2E = 2.0 ** -21
 RADIUS_TOL = 1e-4      # |3 sqrt(lambda) - k| below this (relative to value) may flip
 EDGE_TOL_PX = 2e-3     # rectangle edges within this many pixels of a tile boundary may flip
 XY_TOL_REL = 2e-6      # |x_gpu - x| <= XY_TOL_REL * (|x| + fx) pixels
@@ -63,8 +69,23 @@ def records_from_oracle(pre: dict, splat_dtype) -> np.ndarray:
     r = pre["rect"].astype(np.uint32)
     rec["rect_lo"] = np.where(vis, r[:, 0] | (r[:, 1] << 16), 0)
     rec["rect_hi"] = np.where(vis, r[:, 2] | (r[:, 3] << 16), 0)
-    rec["opacity"] = np.where(vis, pre["opacity"], 0)
+    hx, hy = cull_box(pre)
+    rec["cull_hx"] = np.where(vis, hx * (1 + 2.0 ** -10) + 1.0 / 64, -1.0)
+    rec["cull_hy"] = np.where(vis, hy * (1 + 2.0 ** -10) + 1.0 / 64, -1.0)
+    rec["cull_hx"][vis & (hx < 0)] = -1.0
+    rec["cull_hy"][vis & (hy < 0)] = -1.0
     return rec
+
+
+def cull_box(pre: dict):
+    """Half-extents of the bounding box of the region where alpha = o
+    exp(-d^T Sigma'^-1 d / 2) reaches 1/255: sqrt(2 ln(255 o) Sigma'_xx) and
+    sqrt(2 ln(255 o) Sigma'_yy); -1 where 255 o <= 1 (nowhere)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r2 = 2.0 * np.log(255.0 * pre["opacity"])
+        hx = np.where(r2 > 0, np.sqrt(np.maximum(r2, 0) * pre["cov2d"][:, 0]), -1.0)
+        hy = np.where(r2 > 0, np.sqrt(np.maximum(r2, 0) * pre["cov2d"][:, 2]), -1.0)
+    return hx, hy
 
 
 def conic_from_record(rec: np.ndarray) -> np.ndarray:
@@ -115,8 +136,19 @@ def compare_preprocess(gpu: np.ndarray, pre: dict, cam) -> dict:
     assert np.all(conic_rel <= 1e-4), f"conic relative error {conic_rel.max():.3e}"
     rgb_err = np.abs(np.stack([gpu["r"], gpu["g"], gpu["b"]], 1) - pre["rgb"])[b]
     assert np.all(rgb_err <= 2e-5), f"rgb error {rgb_err.max():.3e}"
-    op_err = np.abs(gpu["opacity"].astype(np.float64) - pre["opacity"])[b]
+    op_err = np.abs(np.exp2(gpu["log2_opacity"].astype(np.float64)) - pre["opacity"])[b]
     assert np.all(op_err <= 1e-6), f"opacity error {op_err.max():.3e}"
+    # the culling box must contain the exact alpha >= 1/255 region, and be tight
+    hx, hy = cull_box(pre)
+    with np.errstate(divide="ignore"):
+        rho_margin = np.abs(np.log(255.0 * pre["opacity"]))
+    firm = b & (rho_margin > 1e-5)
+    for got, want in ((gpu["cull_hx"], hx), (gpu["cull_hy"], hy)):
+        g, w = got[firm].astype(np.float64), want[firm]
+        assert np.all((w < 0) == (g < 0)), "culling box emptiness differs"
+        pos = w >= 0
+        assert np.all(g[pos] >= w[pos] * (1 - 1e-6)), "culling box smaller than the alpha >= 1/255 region"
+        assert np.all(g[pos] <= w[pos] * 1.002 + 0.02), "culling box looser than its stated slack"
     lg_err = np.abs(gpu["log2_opacity"][b].astype(np.float64) - np.log2(pre["opacity"][b]))
     assert np.all(lg_err <= 1e-5 * np.maximum(1.0, np.abs(np.log2(pre["opacity"][b])))), \
         f"log2 opacity error {lg_err.max():.3e}"

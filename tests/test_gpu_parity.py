@@ -12,7 +12,7 @@ import torch
 import paper_2509_25626_gb300 as gs
 from paper_2509_25626_gb300 import SPLAT_DTYPE, SceneTensors
 from parity import (ambiguous_gaussians, check_sorted_output, compare_images, compare_preprocess, flip_tile_mask,
-                    rect_of, records_from_oracle, TAU_ALPHA, TAU_T)
+                    rect_of, records_from_oracle, POS_EPS_E2E, TAU_ALPHA, TAU_T)
 from synth import clustered_scene, orbit_camera, pinhole_camera, tiny_scene, uniform_box_scene, Scene
 
 pytestmark = pytest.mark.gpu
@@ -63,7 +63,8 @@ SMALL = scenes_small()
 def oracle_frames(oracle):
     frames = {}
     for name, sc, cam in SMALL:
-        pre, srt, img = oracle.frame(sc, cam, bg=(0.1, 0.2, 0.3), tau_alpha=TAU_ALPHA, tau_T=TAU_T)
+        pre, srt, img = oracle.frame(sc, cam, bg=(0.1, 0.2, 0.3), tau_alpha=TAU_ALPHA, tau_T=TAU_T,
+                                     pos_eps=POS_EPS_E2E)
         frames[name] = (pre, srt, img)
     return frames
 
@@ -154,7 +155,7 @@ def test_batches_stop_permanently(oracle):
     sh[:, 0, :] = (0.8 - 0.5) / 0.28209479177387814
     sc = Scene(means, np.full((n, 3), -3.0, np.float32), np.tile(np.float32([1, 0, 0, 0]), (n, 1)), logits, sh)
     cam = pinhole_camera(33, 33)
-    pre, srt, img = oracle.frame(sc, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T)
+    pre, srt, img = oracle.frame(sc, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T, pos_eps=POS_EPS_E2E)
     st = SceneTensors.from_scene(sc, DEV)
     sp = gs.preprocess(st, cam)
     _, _, _, m, vals, ranges = gpu_sort(sp, n, cam)
@@ -186,7 +187,7 @@ def test_empty_and_culled_scenes():
 def test_one_pixel_and_ragged_images(oracle):
     for (w, h) in ((1, 1), (17, 1), (1, 33), (31, 47)):
         sc, cam = tiny_scene(80, w * 7 + h, w, h, log_scale=(-2.5, 0.5))
-        pre, srt, img = oracle.frame(sc, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T)
+        pre, srt, img = oracle.frame(sc, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T, pos_eps=POS_EPS_E2E)
         st = SceneTensors.from_scene(sc, DEV)
         sp = gs.preprocess(st, cam)
         keys, vals_np, ranges_np, m, vals, ranges = gpu_sort(sp, sc.n, cam)
@@ -256,7 +257,7 @@ def test_full_size_scene_sampled(oracle):
     compare_preprocess(recs[idx], sub, cam)
     srt = oracle.duplicate_sort(pre, cam)
     rows = (512, 544)  # two tile rows through the middle of the image
-    img = oracle.render(pre, srt, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T, rows=rows)
+    img = oracle.render(pre, srt, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T, rows=rows, pos_eps=POS_EPS_E2E)
     sl = slice(*rows)
     band = {k: (v[:, sl] if k == "color" else v[sl]) for k, v in img.items()}
     g_img = ws_probe.image.cpu().numpy()[:, sl]
@@ -266,5 +267,7 @@ def test_full_size_scene_sampled(oracle):
                        np.any(rect_of(recs) != pre["rect"], axis=1))[0]
     assert np.all(ambiguous_gaussians(pre, cam)[flips]), "a rectangle flipped on a non-ambiguous Gaussian"
     amb = flip_tile_mask(recs, pre, flips, cam, rows=rows)
-    rep = compare_images(g_img, g_T, g_nc, band, exclude=amb)
+    # large image: more evaluations per pixel and larger coordinates widen the
+    # margins; the cap stays a sanity bound on what the exclusion hides
+    rep = compare_images(g_img, g_T, g_nc, band, exclude=amb, max_excluded_frac=0.03)
     print("full size", m, rep)

@@ -27,6 +27,21 @@ constexpr float kLog2e = 1.4426950408889634f;
 // of base to 2 into the inverse-covariance factor.
 constexpr float kWhiten = 0.8493218002880191f;
 
+// Word offsets inside a gs_splat record (16 x 4 bytes).
+namespace rec {
+enum : int {
+    kX = 0, kY = 1, kW00 = 2, kW01 = 3, kW11 = 4, kLog2O = 5, kR = 6, kG = 7, kB = 8, kHx = 9, kHy = 10,
+    kDepth = 11, kTiles = 12, kRectLo = 13, kRectHi = 14, kRadius = 15,
+};
+}  // namespace rec
+
+// Culling box slack: relative and absolute widening of the alpha >= 1/255
+// bounding box (FP32 rounding of the render's exponent is ~1e-5 of it).
+constexpr float kCullRel = 1.0f / 1024.0f;
+constexpr float kCullAbs = 1.0f / 64.0f;
+// log2(255): alpha >= 1/255  <=>  log2_opacity - (u^2 + v^2) >= -log2(255)
+constexpr float kLog2_255 = 7.994353436858858f;
+
 // Camera as the kernels see it (kernel parameter, passed by value).
 struct CamParams {
     float V[12];          // rows 0..2 of the world->camera matrix

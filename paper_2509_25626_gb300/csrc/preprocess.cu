@@ -41,8 +41,8 @@ __device__ __forceinline__ void write_culled(gs_splat *out, float depth) {
     float4 *o = reinterpret_cast<float4 *>(out);
     o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    o[2] = make_float4(0.f, depth, 0.f, 0.f);  // b, depth, radius = 0, tiles = 0
-    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    o[2] = make_float4(0.f, -1.f, -1.f, depth);  // b, cull box empty, depth
+    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);       // tiles = 0, rect 0, radius = 0
 }
 
 __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict__ means,
@@ -185,14 +185,25 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
 
     const float logit = logits[g];
     const float e = expf(-logit);
-    const float opacity = 1.0f / (1.0f + e);
     const float log2_opacity = -log1pf(e) * kLog2e;
+
+    // Bounding box of the alpha >= 1/255 ellipse |W d|^2 <= rho:
+    // half-extents sqrt(rho Sigma'_xx) / k and sqrt(rho Sigma'_yy) / k.
+    const float rho = log2_opacity + kLog2_255;
+    float hx = -1.f, hy = -1.f;
+    if (rho > 0.f) {
+        hx = sqrtf(rho * s00) * (1.0f / kWhiten);
+        hy = sqrtf(rho * s11) * (1.0f / kWhiten);
+        hx = fmaf(hx, kCullRel, hx) + kCullAbs;
+        hy = fmaf(hy, kCullRel, hy) + kCullAbs;
+    }
 
     float4 *o = reinterpret_cast<float4 *>(out + g);
     o[0] = make_float4(x, y, w00, w01);
     o[1] = make_float4(w11, log2_opacity, rgb[0], rgb[1]);
-    o[2] = make_float4(rgb[2], z, __int_as_float((int)radius), __uint_as_float(tiles));
-    o[3] = make_float4(__uint_as_float(x0 | (y0 << 16)), __uint_as_float(x1 | (y1 << 16)), opacity, 0.f);
+    o[2] = make_float4(rgb[2], hx, hy, z);
+    o[3] = make_float4(__uint_as_float(tiles), __uint_as_float(x0 | (y0 << 16)), __uint_as_float(x1 | (y1 << 16)),
+                       __int_as_float((int)radius));
 }
 
 }  // namespace

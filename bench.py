@@ -42,8 +42,34 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-backward", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-multiview", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
     return p.parse_args()
+
+
+def rank_pose(k: int, world: int, rank: int, n_poses: int) -> int:
+    """Pose rendered by `rank` at step k: ranks interleave over the orbit, so
+    the N replicas render disjoint poses each step (weak scaling, no data
+    exchange)."""
+    return (k * world + rank) % n_poses
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest `value` over all ranks (the job's time is its slowest
+    rank's); identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time."""
+    return units_per_rank * world / (max_ms / 1000.0)
 
 
 def measured_peaks():
@@ -237,7 +263,7 @@ def main():
         vis.append(int((r.splats.view(torch.int32)[:, 12] > 0).sum().item()))  # tiles_touched
 
     stream = torch.cuda.current_stream(dev)
-    pose_of = lambda k: (k * world + rank) % P
+    pose_of = lambda k: rank_pose(k, world, rank, P)
 
     for k in range(args.warmup):
         r.frame(st, cams[pose_of(k)])
@@ -271,11 +297,8 @@ def main():
     rend_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
     m_last, over = r.instances()
     assert not over, "instance capacity overflow during the timed region"
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    fps = args.steps * world / (t_ms / 1000.0)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    fps = whole_job_rate(args.steps, world, t_ms)
 
     # end to end through the public API: scene from pinned host memory each
     # step, image back to pinned host memory
@@ -303,12 +326,8 @@ def main():
         e2.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        te = s2.elapsed_time(e2)
-        if world > 1:
-            tt = torch.tensor([te], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = dict(value=args.steps * world / (te / 1000.0), unit="frames/s", h2d_bytes_per_step=h2d,
+        te = max_over_ranks(s2.elapsed_time(e2), world, dev)
+        e2e = dict(value=whole_job_rate(args.steps, world, te), unit="frames/s", h2d_bytes_per_step=h2d,
                    d2h_bytes_per_step=d2h)
 
     # roofline of the dominant kernel (the render: FP32 issue bound)
@@ -341,12 +360,18 @@ def main():
         sort=dict(ms=sort_ms, instances=ms_mean),
         render=dict(ms=rend_ms, evals=evals_mean, tflops=render_tflops),
     )
+    # kernels per frame: preprocess; compact, 4 depth radix passes, offsets,
+    # duplicate, one radix pass per 8 bits of tile id, ranges; render
     tb = max(0, math.ceil(math.log2(T))) if T > 1 else 0
-    launches_per_frame = 1 + 17 + 2 + 3 * ((tb + 7) // 8) + 1
+    launches_per_frame = 1 + (1 + 4 + 1 + 1 + max(1, (tb + 7) // 8) + 1) + 1
 
     serving = None
     if rank == 0 and not args.no_serving:
         serving = measure_serving(gs, dev)
+
+    multiview = None
+    if rank == 0 and not args.no_multiview:
+        multiview = measure_multiview(gs, dev)
 
     backward = None
     if not args.no_backward:
@@ -369,7 +394,8 @@ def main():
                         instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
                         m_cap=m_cap, parallelism=f"replicas{world}",
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
-            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, serving=serving, backward=backward,
+            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, serving=serving, multiview=multiview,
+            backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,
             peaks_src=peaks["src"],
         )
@@ -414,6 +440,87 @@ def measure_serving(gs, dev, rate: float = 200.0, duration: float = 2.5):
                scenes={name: n for name, n, _ in specs}, resolutions=[f"{w}x{h}" for w, h in res],
                batches=int(srv.stats["batches"]), overflow_or_timeout=int(srv.stats["overflow_or_timeout"]))
     return out
+
+
+def measure_multiview(gs, dev, steps: int = 5):
+    """Load-imbalance workload: 6M Gaussians, half packed in an occluding
+    slab, 8 views at 3840x2160.  Per step: the 8 views' preprocess and sort,
+    then their renders in ONE persistent launch (gs_render_batch); compared
+    with the same renders as 8 separate gs_render launches."""
+    import ctypes
+    import torch
+    from paper_2509_25626_gb300 import _lib as L
+    from paper_2509_25626_gb300 import serve as S
+    from synth import CONFIGS
+    wl = CONFIGS["slab_6m_3840x2160x8"]
+    scene = wl["scene"]()
+    cams = wl["cameras"]()
+    st = gs.SceneTensors.from_scene(scene, dev)
+    ms = []
+    for cam in cams:
+        sp = gs.preprocess(st, cam)
+        _, _, _, m, _ = gs.sort(sp, st.n, cam, 1 << 27)
+        ms.append(m)
+        del sp
+    rs = [gs.Renderer(st.n, cam.width, cam.height, int(max(ms) * 1.05) + 4096, dev) for cam in cams]
+    srv = S.Server({}, max_batch=len(cams), device=dev)
+
+    class _Req:
+        def __init__(self, cam):
+            self.cam, self.bg = cam, (0.0, 0.0, 0.0)
+
+    class _Slot:
+        def __init__(self, r, cam):
+            self.splats, self.vals, self.ranges = r.splats, r.vals, r.ranges
+            self.image, self.final_T, self.n_contrib = r.image, r.final_T, r.n_contrib
+            self.tiles = gs.num_tiles(cam)
+
+    batch = [(_Req(c), _Slot(r, c)) for r, c in zip(rs, cams)]
+    tiles = srv._write_desc(batch)
+    srv.desc_dev.copy_(srv.desc_host)
+    stream = torch.cuda.current_stream(dev)
+    sptr = ctypes.c_void_p(int(stream.cuda_stream))
+
+    def front():
+        for r, cam in zip(rs, cams):
+            gs.preprocess(st, cam, r.splats)
+            gs.sort(r.splats, st.n, cam, r.m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
+
+    def batched():
+        L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
+                                        ctypes.c_void_p(srv.counter.data_ptr()), 0, sptr), "gs_render_batch")
+
+    def separate():
+        for r, cam in zip(rs, cams):
+            gs.render(r.splats, r.vals, r.ranges, cam, (0.0, 0.0, 0.0), r.image, r.final_T, r.n_contrib)
+
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fn in (("batched", batched), ("separate", separate)):
+        front()
+        fn()
+        torch.cuda.synchronize(dev)
+        t_front = t_render = 0.0
+        for _ in range(steps):
+            a, b, c = E(), E(), E()
+            a.record(stream)
+            front()
+            b.record(stream)
+            fn()
+            c.record(stream)
+            torch.cuda.synchronize(dev)
+            t_front += a.elapsed_time(b)
+            t_render += b.elapsed_time(c)
+        res[name] = dict(render_ms=t_render / steps, preprocess_sort_ms=t_front / steps,
+                         views_per_s=len(cams) * 1000.0 / ((t_front + t_render) / steps))
+    lens = []
+    for r in rs:
+        rg = r.ranges.to(torch.int64)
+        lens.append((rg[:, 1] - rg[:, 0]).cpu())
+    lens = torch.cat(lens).float()
+    return dict(workload="slab_6m_3840x2160x8", gaussians=st.n, views=len(cams), tiles=int(tiles),
+                instances_mean=float(sum(ms) / len(ms)), tile_list_mean=float(lens.mean()),
+                tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), **res)
 
 
 def measure_backward(gs, dev, steps: int, warmup: int):

@@ -250,17 +250,19 @@ def main():
     m_cap = int(max(ms) * 1.05) + 4096
     r = gs.Renderer(n, W, H, m_cap, dev)
 
-    # evaluations per pose (untimed), the render's work count
-    evals = []
+    # evaluations per pose (untimed), the render's work count, and the
+    # per-tile block cycles (load balance)
+    evals, tile_stats = [], []
     for cam in cams:
         gs.preprocess(st, cam, r.splats)
         gs.sort(r.splats, n, cam, m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
-        _, _, _, ne = gs.render_workload(r.splats, r.vals, r.ranges, cam)
+        _, _, _, ne, cyc = gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)
         evals.append(int(ne.to(torch.int64).sum().item()))
+        tile_stats.append(tile_cycle_stats(cyc))
     vis = []
     for cam in cams[:1]:
         gs.preprocess(st, cam, r.splats)
-        vis.append(int((r.splats.view(torch.int32)[:, 12] > 0).sum().item()))  # tiles_touched
+        vis.append(int((r.splats.view(torch.int32)[:, 13] > 0).sum().item()))  # tiles_touched
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: rank_pose(k, world, rank, P)
@@ -358,7 +360,8 @@ def main():
     kernels = dict(
         preprocess=dict(ms=pre_ms, bytes=pre_bytes, gbs=pre_gbs, frac_hbm=pre_gbs / peaks["hbm_gbs"]),
         sort=dict(ms=sort_ms, instances=ms_mean),
-        render=dict(ms=rend_ms, evals=evals_mean, tflops=render_tflops),
+        render=dict(ms=rend_ms, evals=evals_mean, tflops=render_tflops,
+                    tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
     )
     # kernels per frame: preprocess; compact, 4 depth radix passes, offsets,
     # duplicate, one radix pass per 8 bits of tile id, ranges; render
@@ -403,6 +406,15 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def tile_cycle_stats(cyc) -> dict:
+    """Per-tile block cycles (gs_render_workload): mean, p99, max, max/mean."""
+    import torch
+    c = cyc.reshape(-1).to(torch.float64)
+    mean = float(c.mean())
+    return dict(mean=mean, p99=float(torch.quantile(c, 0.99)), max=float(c.max()),
+                max_over_mean=float(c.max()) / max(mean, 1.0), sum=float(c.sum()))
 
 
 def measure_serving(gs, dev, rate: float = 200.0, duration: float = 2.5):
@@ -513,14 +525,16 @@ def measure_multiview(gs, dev, steps: int = 5):
             t_render += b.elapsed_time(c)
         res[name] = dict(render_ms=t_render / steps, preprocess_sort_ms=t_front / steps,
                          views_per_s=len(cams) * 1000.0 / ((t_front + t_render) / steps))
-    lens = []
-    for r in rs:
+    lens, cycs = [], []
+    for r, cam in zip(rs, cams):
         rg = r.ranges.to(torch.int64)
         lens.append((rg[:, 1] - rg[:, 0]).cpu())
+        cycs.append(gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)[4].reshape(-1).cpu())
     lens = torch.cat(lens).float()
+    tc = tile_cycle_stats(torch.cat(cycs))
     return dict(workload="slab_6m_3840x2160x8", gaussians=st.n, views=len(cams), tiles=int(tiles),
                 instances_mean=float(sum(ms) / len(ms)), tile_list_mean=float(lens.mean()),
-                tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), **res)
+                tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), tile_cycles=tc, **res)
 
 
 def measure_backward(gs, dev, steps: int, warmup: int):

@@ -89,12 +89,12 @@ typedef struct gs_splat {
     float log2_opacity;       /* log2(sigmoid(logit)) */
     float r, g, b;            /* SH colour + 0.5, clamped at 0 */
     float cull_hx, cull_hy;   /* half-extents of the alpha >= 1/255 region */
+    int32_t radius;           /* ceil(3 sqrt(lambda_max(Sigma'))) pixels */
     float depth;              /* view-space z, FP32; its bits form the sort key */
     uint32_t tiles_touched;   /* (x1 - x0) (y1 - y0) */
     uint32_t rect_lo;         /* x0 | y0 << 16, tile rectangle, inclusive */
     uint32_t rect_hi;         /* x1 | y1 << 16, exclusive */
-    int32_t radius;           /* ceil(3 sqrt(lambda_max(Sigma'))) pixels */
-} gs_splat;
+} gs_splat;  /* the last four words (the sort's inputs) share one 16-byte vector */
 
 /* Section II-B (1), projection step.  One thread per Gaussian:
  *   z = V.[m, 1] (FP32, fmaf(V22, mz, fmaf(V21, my, fmaf(V20, mx, V23))));
@@ -190,12 +190,15 @@ int gs_render_backward(const gs_scene *scene, const gs_camera *cam, const gs_spl
  * pixel stopped (the stopping splat included; all of the tile's splats if it
  * never stopped): n_eval [H][W] uint32, device.  Its sum over the image is
  * the "Gaussian-pixel evaluations" work count, the per-thread workload
- * measure of the paper's Table III.  Slightly slower than gs_render; meant
- * for workload characterisation, not for the hot path.
- * Errors: as gs_render. */
+ * measure of the paper's Table III.  tile_cycles (device uint32
+ * [tiles_y][tiles_x], or NULL): SM clock cycles the block spent on each
+ * tile, from its first instruction to its last store (saturated at
+ * 2^32 - 1) -- the per-block load-balance measure of Section IV-C.
+ * Slightly slower than gs_render; meant for workload characterisation, not
+ * for the hot path.  Errors: as gs_render. */
 int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
-                       void *stream);
+                       uint32_t *tile_cycles, void *stream);
 
 /* gs_sort without a caller-provided workspace, for callers that cannot
  * allocate device memory: code running inside another framework's memory
@@ -204,7 +207,7 @@ int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint3
  * counterpart; this is a deployment convenience.
  *
  * Same arguments, results and errors as gs_sort minus the workspace.  The
- * scratch is a fixed 36 MiB array inside the library, which every GPU that
+ * scratch is a fixed 38 MiB array inside the library, which every GPU that
  * loads the library holds until the process exits; it bounds the sizes:
  * n <= GS_SORT_STATIC_MAX_GAUSSIANS and m_cap <= GS_SORT_STATIC_MAX_INSTANCES,
  * else GS_ERR_TOO_LARGE (checked before any GPU work).  The call allocates

@@ -40,8 +40,8 @@ class GsScene(ctypes.Structure):
 # numpy view of one gs_splat record (64 bytes)
 SPLAT_DTYPE = np.dtype([
     ("x", "<f4"), ("y", "<f4"), ("w00", "<f4"), ("w01", "<f4"), ("w11", "<f4"), ("log2_opacity", "<f4"),
-    ("r", "<f4"), ("g", "<f4"), ("b", "<f4"), ("cull_hx", "<f4"), ("cull_hy", "<f4"), ("depth", "<f4"),
-    ("tiles_touched", "<u4"), ("rect_lo", "<u4"), ("rect_hi", "<u4"), ("radius", "<i4"),
+    ("r", "<f4"), ("g", "<f4"), ("b", "<f4"), ("cull_hx", "<f4"), ("cull_hy", "<f4"), ("radius", "<i4"),
+    ("depth", "<f4"), ("tiles_touched", "<u4"), ("rect_lo", "<u4"), ("rect_hi", "<u4"),
 ])
 assert SPLAT_DTYPE.itemsize == 64
 
@@ -80,7 +80,7 @@ def lib():
         L.gs_sort_static.restype = ctypes.c_int
         L.gs_render_batch.argtypes = [P, P, ctypes.c_int32, P]
         L.gs_render_batch.restype = ctypes.c_int
-        L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P]
+        L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P, P]
         L.gs_backward_workspace_bytes.argtypes = [c_int64]
         L.gs_backward_workspace_bytes.restype = c_size_t
         L.gs_render_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P, P,

@@ -188,19 +188,27 @@ def render(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, 
 
 
 def render_workload(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
-                    stream=None):
-    """gs_render_workload: (image, final_T, n_contrib, n_eval [H, W] int32)."""
+                    stream=None, tile_cycles: bool = False):
+    """gs_render_workload: (image, final_T, n_contrib, n_eval [H, W] int32),
+    plus the per-tile SM cycles [tiles_y, tiles_x] int64 if tile_cycles."""
     dev = splats.device
     H, W = int(cam.height), int(cam.width)
     out_color = torch.empty((3, H, W), dtype=torch.float32, device=dev)
     final_T = torch.empty((H, W), dtype=torch.float32, device=dev)
     n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
     n_eval = torch.empty((H, W), dtype=torch.int32, device=dev)
+    cyc = None
+    if tile_cycles:
+        cyc = torch.zeros(((H + 15) // 16, (W + 15) // 16), dtype=torch.int32, device=dev)
     c = camera_struct(cam)
     bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
     code = L.lib().gs_render_workload(_ptr(splats), _ptr(vals), _ptr(ranges), ctypes.byref(c), bgc,
-                                      _ptr(out_color), _ptr(final_T), _ptr(n_contrib), _ptr(n_eval), _stream(stream))
+                                      _ptr(out_color), _ptr(final_T), _ptr(n_contrib), _ptr(n_eval),
+                                      _ptr(cyc), _stream(stream))
     L.check(code, "gs_render_workload")
+    if tile_cycles:
+        # stored as uint32 bit patterns
+        return out_color, final_T, n_contrib, n_eval, cyc.to(torch.int64) & 0xFFFFFFFF
     return out_color, final_T, n_contrib, n_eval
 
 

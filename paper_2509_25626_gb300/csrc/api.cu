@@ -13,7 +13,8 @@
 namespace gs {
 
 cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat *out, cudaStream_t stream);
-cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, cudaStream_t st);
+cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
+                              uint32_t num_tiles, cudaStream_t st);
 cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
                              uint32_t num_tiles, uint64_t *keys, uint32_t *vals, uint32_t *ranges, cudaStream_t st);
 cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
@@ -23,7 +24,7 @@ cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, cons
 cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
-                          uint32_t *n_eval, cudaStream_t stream);
+                          uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream);
 
 static thread_local char g_cuda_err[256] = "no CUDA error recorded";
 
@@ -93,7 +94,8 @@ int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *k
     cudaStream_t st = (cudaStream_t)stream;
     SortWs ws;
     carve_sort_ws(static_cast<char *>(workspace), n, m_cap, num_tiles, &ws);
-    cudaError_t e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, st);
+    const int tiles_x = (cam->width + kTile - 1) / kTile;
+    cudaError_t e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, tiles_x, (uint32_t)num_tiles, st);
     if (e != cudaSuccess) return cuda_status(e);
     if (m_out) {
         SortHeader h;
@@ -104,7 +106,6 @@ int gs_sort(const gs_splat *splats, int64_t n, const gs_camera *cam, uint64_t *k
         if (h.timeout) return GS_ERR_TIMEOUT;
         if (h.m_total > (uint64_t)m_cap) return GS_ERR_CAPACITY;
     }
-    const int tiles_x = (cam->width + kTile - 1) / kTile;
     return cuda_status(launch_sort_back(splats, n, ws, (uint64_t)m_cap, tiles_x, (uint32_t)num_tiles, keys, vals,
                                         ranges, st));
 }
@@ -123,7 +124,7 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream) {
 
 static int render_common(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
-                         uint32_t *n_eval, void *stream) {
+                         uint32_t *n_eval, uint32_t *tile_cycles, void *stream) {
     if (!camera_ok(cam) || !bg || !ranges || !aligned(ranges, 8)) return GS_ERR_INVALID_ARG;
     if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
     if (!out_color || !final_T || !n_contrib || !aligned(out_color, 4) || !aligned(final_T, 4) ||
@@ -133,19 +134,19 @@ static int render_common(const gs_splat *splats, const uint32_t *vals, const uin
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
     return cuda_status(launch_render(splats, vals, ranges, make_cam_params(*cam), bg, out_color, final_T, n_contrib,
-                                     n_eval, (cudaStream_t)stream));
+                                     n_eval, tile_cycles, (cudaStream_t)stream));
 }
 
 int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
               const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream) {
-    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, stream);
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, nullptr, stream);
 }
 
 int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
-                       void *stream) {
-    if (!n_eval || !aligned(n_eval, 4)) return GS_ERR_INVALID_ARG;
-    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, n_eval, stream);
+                       uint32_t *tile_cycles, void *stream) {
+    if (!n_eval || !aligned(n_eval, 4) || (tile_cycles && !aligned(tile_cycles, 4))) return GS_ERR_INVALID_ARG;
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, n_eval, tile_cycles, stream);
 }
 
 int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t grid, void *stream) {

@@ -31,7 +31,7 @@ constexpr float kWhiten = 0.8493218002880191f;
 namespace rec {
 enum : int {
     kX = 0, kY = 1, kW00 = 2, kW01 = 3, kW11 = 4, kLog2O = 5, kR = 6, kG = 7, kB = 8, kHx = 9, kHy = 10,
-    kDepth = 11, kTiles = 12, kRectLo = 13, kRectHi = 14, kRadius = 15,
+    kRadius = 11, kDepth = 12, kTiles = 13, kRectLo = 14, kRectHi = 15,
 };
 }  // namespace rec
 

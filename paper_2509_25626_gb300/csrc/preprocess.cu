@@ -41,8 +41,8 @@ __device__ __forceinline__ void write_culled(gs_splat *out, float depth) {
     float4 *o = reinterpret_cast<float4 *>(out);
     o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    o[2] = make_float4(0.f, -1.f, -1.f, depth);  // b, cull box empty, depth
-    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);       // tiles = 0, rect 0, radius = 0
+    o[2] = make_float4(0.f, -1.f, -1.f, 0.f);     // b, cull box empty, radius = 0
+    o[3] = make_float4(depth, 0.f, 0.f, 0.f);     // depth, tiles = 0, rect 0
 }
 
 __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict__ means,
@@ -201,9 +201,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     float4 *o = reinterpret_cast<float4 *>(out + g);
     o[0] = make_float4(x, y, w00, w01);
     o[1] = make_float4(w11, log2_opacity, rgb[0], rgb[1]);
-    o[2] = make_float4(rgb[2], hx, hy, z);
-    o[3] = make_float4(__uint_as_float(tiles), __uint_as_float(x0 | (y0 << 16)), __uint_as_float(x1 | (y1 << 16)),
-                       __int_as_float((int)radius));
+    o[2] = make_float4(rgb[2], hx, hy, __int_as_float((int)radius));
+    o[3] = make_float4(z, __uint_as_float(tiles), __uint_as_float(x0 | (y0 << 16)), __uint_as_float(x1 | (y1 << 16)));
 }
 
 }  // namespace

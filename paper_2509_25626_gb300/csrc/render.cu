@@ -53,8 +53,10 @@ __device__ __forceinline__ void blend(Pixel &p, float alpha, float r, float g, f
 // kCount: also write, per pixel, how many splats were evaluated before the
 // pixel stopped (the stopping one included; the whole list if it never
 // stopped) -- the work measure of the paper's workload characterisation
-// (Table III).  It follows from the stopping position, so the loop is the
-// same in both instantiations.
+// (Table III) -- and, if tile_cycles is set, the SM clock cycles the block
+// spent on the tile (the per-block load-balance measure of Section IV-C).
+// Both follow from state the loop keeps anyway, so the loop is the same in
+// both instantiations.
 struct RenderSmem {
     StagedA a[kBatch];
     StagedB b[kBatch];
@@ -65,13 +67,15 @@ struct RenderSmem {
 
 // Renders one tile with the whole block.  Every thread must call it; it
 // begins and ends with block-wide barriers, so the shared memory may be
-// reused for the next tile.
+// reused for the next tile.  The job's pointers and sizes are read where
+// they are used, not held in registers: the batch kernel keeps its job in
+// shared memory, the single-image kernel in its parameters.
 template <bool kCount>
-__device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__restrict__ splats,
-                                            const uint32_t *__restrict__ vals, const uint2 range, int tile,
-                                            int width, int height, int tiles_x, float bg_r, float bg_g, float bg_b,
-                                            float *__restrict__ out_color, float *__restrict__ final_T,
-                                            uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ n_eval) {
+__device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job &job, const uint2 range, int tile,
+                                            uint32_t *__restrict__ n_eval, uint32_t *__restrict__ tile_cycles) {
+    long long t_start = 0;
+    if (kCount) t_start = clock64();
+    const int width = job.width, tiles_x = (width + kTile - 1) / kTile;
     StagedA *s_a = sm.a;
     StagedB *s_b = sm.b;
     float *s_c = sm.c;
@@ -83,7 +87,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__re
     const int bx0 = tx * kTile + (int)(warp & 1u) * 8, by0 = ty * kTile + (int)(warp >> 1) * 8;
     const int px = bx0 + 2 * (int)(lane & 3u), py = by0 + (int)(lane >> 2);
     const float pxf = (float)px, pyf = (float)py;
-    const bool in0 = px < width && py < height, in1 = px + 1 < width && py < height;
+    const bool in0 = px < width && py < job.height, in1 = px + 1 < width && py < job.height;
     Pixel p0{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in0};
     Pixel p1{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in1};
 
@@ -100,8 +104,9 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__re
             const uint32_t i = base + (uint32_t)k;
             uint32_t m = 0;
             if (i < range.y) {
-                const float4 *src = reinterpret_cast<const float4 *>(splats + vals[i]);
-                const float4 a = src[0], b = src[1], c = src[2];
+                // read-only path: the batch kernel takes these pointers from memory
+                const float4 *src = reinterpret_cast<const float4 *>(job.splats + __ldg(job.vals + i));
+                const float4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
                 s_a[k] = StagedA{a.x, a.y, a.z, a.w};
                 s_b[k] = StagedB{b.x, b.y, b.z, b.w};
                 s_c[k] = c.x;
@@ -152,15 +157,17 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__re
         }
     }
 
-    const size_t plane = (size_t)width * height;
+    const size_t plane = (size_t)width * job.height;
     const uint32_t len = range.y - range.x;
+    float *__restrict__ out_color = job.out_color;
+    const float bg_r = job.bg[0], bg_g = job.bg[1], bg_b = job.bg[2];
     if (in0) {
         const size_t pix = (size_t)py * width + px;
         out_color[pix] = fmaf(p0.T, bg_r, p0.c0);
         out_color[plane + pix] = fmaf(p0.T, bg_g, p0.c1);
         out_color[2 * plane + pix] = fmaf(p0.T, bg_b, p0.c2);
-        final_T[pix] = p0.T;
-        n_contrib[pix] = p0.last;
+        job.final_T[pix] = p0.T;
+        job.n_contrib[pix] = p0.last;
         if (kCount) n_eval[pix] = p0.stop ? p0.stop : len;
     }
     if (in1) {
@@ -168,54 +175,80 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_splat *__re
         out_color[pix] = fmaf(p1.T, bg_r, p1.c0);
         out_color[plane + pix] = fmaf(p1.T, bg_g, p1.c1);
         out_color[2 * plane + pix] = fmaf(p1.T, bg_b, p1.c2);
-        final_T[pix] = p1.T;
-        n_contrib[pix] = p1.last;
+        job.final_T[pix] = p1.T;
+        job.n_contrib[pix] = p1.last;
         if (kCount) n_eval[pix] = p1.stop ? p1.stop : len;
     }
     __syncthreads();  // shared memory free for the next tile
+    if (kCount && tile_cycles != nullptr && threadIdx.x == 0) {
+        const long long dt = clock64() - t_start;
+        tile_cycles[tile] = dt < 0 ? 0u : (dt > 0xffffffffll ? 0xffffffffu : (uint32_t)dt);
+    }
 }
 
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads) render_kernel(const gs_splat *__restrict__ splats,
                                                           const uint32_t *__restrict__ vals,
                                                           const uint2 *__restrict__ ranges, int width, int height,
-                                                          int tiles_x, float bg_r, float bg_g, float bg_b,
+                                                          float bg_r, float bg_g, float bg_b,
                                                           float *__restrict__ out_color,
                                                           float *__restrict__ final_T,
                                                           uint32_t *__restrict__ n_contrib,
-                                                          uint32_t *__restrict__ n_eval) {
+                                                          uint32_t *__restrict__ n_eval,
+                                                          uint32_t *__restrict__ tile_cycles) {
     __shared__ RenderSmem sm;
-    render_tile<kCount>(sm, splats, vals, ranges[blockIdx.x], blockIdx.x, width, height, tiles_x, bg_r, bg_g, bg_b,
-                        out_color, final_T, n_contrib, n_eval);
+    gs_render_job job;
+    job.splats = splats;
+    job.vals = vals;
+    job.ranges = nullptr;
+    job.out_color = out_color;
+    job.final_T = final_T;
+    job.n_contrib = n_contrib;
+    job.width = width;
+    job.height = height;
+    job.bg[0] = bg_r;
+    job.bg[1] = bg_g;
+    job.bg[2] = bg_b;
+    job.tile_begin = 0;
+    render_tile<kCount>(sm, job, ranges[blockIdx.x], blockIdx.x, n_eval, tile_cycles);
 }
 
 // Persistent render of many jobs (requests): blocks pull work items -- one
 // (job, tile) each, numbered through the jobs' tile_begin prefix -- from an
-// atomic counter until all are taken.  The job table and its counts live in
-// device memory, so one captured launch serves any batch.
-__global__ void __launch_bounds__(kThreads) render_batch_kernel(const gs_render_batch_desc *__restrict__ desc,
+// atomic counter until all are taken.  Each block asks for its next item
+// when it starts the current one, so the atomic's round trip overlaps the
+// blend.  The job table and its counts live in device memory, so one
+// captured launch serves any batch.  Held to the register count of
+// render_kernel so as many blocks stay resident per SM.
+__global__ void __launch_bounds__(kThreads, 10) render_batch_kernel(const gs_render_batch_desc *__restrict__ desc,
                                                                 uint32_t *__restrict__ counter) {
     __shared__ RenderSmem sm;
+    __shared__ gs_render_job s_job;
     __shared__ uint32_t s_w;
+    static_assert(sizeof(gs_render_job) % 4 == 0 && sizeof(gs_render_job) / 4 <= kThreads, "job copy");
     const int n_jobs = desc->n_jobs;
     const uint32_t total = desc->total_tiles;
-    for (;;) {
-        if (threadIdx.x == 0) s_w = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t w = s_w;
-        __syncthreads();
-        if (w >= total) break;
+    if (threadIdx.x == 0) s_w = atomicAdd(counter, 1u);
+    __syncthreads();
+    for (uint32_t w = s_w; w < total;) {
+        uint32_t next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
         int lo = 0, hi = n_jobs;  // last job with tile_begin <= w
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (desc->jobs[mid].tile_begin <= w) lo = mid; else hi = mid;
         }
-        const gs_render_job &job = desc->jobs[lo];
-        const int tiles_x = (job.width + kTile - 1) / kTile;
-        const int tile = (int)(w - job.tile_begin);
-        render_tile<false>(sm, job.splats, job.vals, reinterpret_cast<const uint2 *>(job.ranges)[tile], tile,
-                           job.width, job.height, tiles_x, job.bg[0], job.bg[1], job.bg[2], job.out_color,
-                           job.final_T, job.n_contrib, nullptr);
+        // the previous tile ended with a barrier, so s_job is free
+        if (threadIdx.x < sizeof(gs_render_job) / 4)
+            reinterpret_cast<uint32_t *>(&s_job)[threadIdx.x] =
+                reinterpret_cast<const uint32_t *>(&desc->jobs[lo])[threadIdx.x];
+        __syncthreads();
+        const int tile = (int)(w - s_job.tile_begin);
+        render_tile<false>(sm, s_job, reinterpret_cast<const uint2 *>(s_job.ranges)[tile], tile, nullptr, nullptr);
+        // render_tile ended with a barrier: nobody reads s_w any more
+        if (threadIdx.x == 0) s_w = next;
+        __syncthreads();
+        w = s_w;
     }
 }
 
@@ -223,16 +256,16 @@ __global__ void __launch_bounds__(kThreads) render_batch_kernel(const gs_render_
 
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
-                          uint32_t *n_eval, cudaStream_t stream) {
+                          uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream) {
     const int num_tiles = cam.tiles_x * cam.tiles_y;
     if (n_eval)
         render_kernel<true><<<num_tiles, kThreads, 0, stream>>>(
-            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, cam.tiles_x, bg[0], bg[1],
-            bg[2], out_color, final_T, n_contrib, n_eval);
+            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, bg[0], bg[1],
+            bg[2], out_color, final_T, n_contrib, n_eval, tile_cycles);
     else
         render_kernel<false><<<num_tiles, kThreads, 0, stream>>>(
-            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, cam.tiles_x, bg[0], bg[1],
-            bg[2], out_color, final_T, n_contrib, nullptr);
+            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, bg[0], bg[1],
+            bg[2], out_color, final_T, n_contrib, nullptr, nullptr);
     return cudaGetLastError();
 }
 

@@ -4,30 +4,33 @@
 // The sorted order is that of a stable sort of the 64-bit keys
 // (tile << 32 | float_bits(depth)) over instances emitted in (Gaussian id,
 // row-major tile) order.  It is reached in fewer passes over less data:
-//   1. compact   visible splats, id order kept; FP32 depth bits by id; the
-//                digit histograms of the depth sort         (one look-back scan)
+//   1. compact   visible splats, id order kept; FP32 depth bits and tile
+//                rectangles by id; the digit counts of the depth sort and of
+//                the tile sort (the latter from rectangle corners alone)
+//                                                           (one look-back scan)
 //   2. depth     stable LSD radix sort of (depth bits, id) over the visible
 //                splats, 4 x 8-bit passes                   (one kernel per pass)
 //   3. offsets   exclusive scan of tiles_touched in depth order -> M and each
 //                splat's first instance                     (one look-back scan)
-//   4. dup       instances in (depth, id, row-major tile) order as 32-bit
-//                tile ids + ids, balanced by instance; the tile digit histograms
-//   5. tiles     stable LSD radix sort on the ceil(log2 T) tile bits, the last
-//                pass writing the full 64-bit keys          (one kernel per pass)
-//   6. ranges    per tile, binary search of its first and last key
-// Within a tile, step 5 keeps step 4's (depth, id) order, which is exactly
-// the tie-broken key order.
+//   4. dup+tile  instances generated in (depth, id, row-major tile) order,
+//                balanced by instance, and ranked at once by the first tile
+//                digit; then one radix pass per further digit, the last
+//                writing the full 64-bit keys
+//   5. ranges    per tile, binary search of its first and last key
+// The tile passes sort the byte-aligned key ty << 8k | tx (k bytes hold tx),
+// which orders like the row-major id ty * tiles_x + tx; within a tile they
+// keep step 4's (depth, id) order, which is exactly the tie-broken key order.
 //
 // Radix passes are single-kernel ("onesweep"): every digit's global total is
-// known beforehand (steps 1 and 4 count them), and each block learns the
-// count of its digit in all earlier blocks by decoupled look-back: it
-// publishes its own count, then walks back over its predecessors' published
-// counts until one carries an inclusive prefix.  Blocks take their index from
-// an atomic counter in launch order, so a block only waits on blocks that
-// are already running; every wait is bounded (1 s of %globaltimer), after
-// which the block records a timeout in the header and goes on (results are
-// then invalid and gs_sort_status reports GS_ERR_TIMEOUT).  All counts stay
-// on the device.
+// known beforehand (step 1 counts them), and each block learns the count of
+// its digit in all earlier blocks by decoupled look-back: it publishes its
+// own count, then walks back over its predecessors' published counts until
+// one carries an inclusive prefix.  Blocks take their index from an atomic
+// counter in launch order, so a block only waits on blocks that are already
+// running; every wait is bounded (1 s of %globaltimer), after which the
+// block records a timeout in the header and goes on (results are then
+// invalid and gs_sort_status reports GS_ERR_TIMEOUT).  All counts stay on
+// the device.
 #include "common.cuh"
 #include "sort_ws.h"
 
@@ -37,6 +40,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kIpt = kSortTileItems / kThreads;  // 16 items per thread
+constexpr int kDepthIpt = kDepthItems / kThreads;  // items per thread in the depth passes
 constexpr int kBins = 256;
 
 constexpr uint64_t kFlagAgg = 1ull << 62;        // block aggregate published
@@ -45,10 +49,6 @@ constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 enum Counter { kCtrCompact = 0, kCtrDepth = 1, kCtrOffsets = 5, kCtrTiles = 6 };
-
-__device__ __forceinline__ uint32_t splat_word(const gs_splat *s, uint32_t g, int w) {
-    return reinterpret_cast<const uint32_t *>(s + g)[w];
-}
 
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
     uint64_t v;
@@ -189,44 +189,98 @@ __device__ __forceinline__ uint64_t block_exclusive_scan64(uint64_t v, uint64_t 
     return res;
 }
 
+// --- tile digit counts from rectangles ---------------------------------------
+// Adds `mult` (mod 2^32: negative counts subtract) to the digit
+// (v >> shift) & 255 of every v in [lo, hi), on a 257-entry difference array
+// (count[d] = diff[0] + ... + diff[d]).  Coordinates are < 2^16, so a digit
+// at shift 8 never wraps.
+__device__ __forceinline__ void add_digit_range(uint32_t *diff, uint32_t lo, uint32_t hi, int shift, uint32_t mult) {
+    if (hi <= lo || mult == 0u) return;
+    if (shift == 0) {
+        const uint32_t len = hi - lo, full = len >> 8, rem = len & 0xffu, a = lo & 0xffu;
+        if (full) atomicAdd(&diff[0], full * mult);  // every digit, `full` times
+        if (rem) {
+            atomicAdd(&diff[a], mult);
+            if (a + rem <= (uint32_t)kBins) {
+                atomicSub(&diff[a + rem], mult);
+            } else {
+                atomicAdd(&diff[0], mult);
+                atomicSub(&diff[a + rem - kBins], mult);
+            }
+        }
+    } else {
+        for (uint32_t v = lo >> shift; v <= ((hi - 1u) >> shift); ++v) {
+            const uint32_t v0 = v << shift, v1 = (v + 1u) << shift;
+            const uint32_t c = (min(hi, v1) - max(lo, v0)) * mult;
+            atomicAdd(&diff[v & 0xffu], c);
+            atomicSub(&diff[(v & 0xffu) + 1u], c);
+        }
+    }
+}
+
+// The digit counts of the instances of tiles [x0, x1) x [y0, y1), times mult.
+__device__ __noinline__ void add_rect_digits(uint32_t (*diff)[kBins + 1], const TileKeyLayout &l, uint32_t x0,
+                                                uint32_t x1, uint32_t y0, uint32_t y1, uint32_t mult) {
+    if (x1 <= x0 || y1 <= y0) return;
+    for (int b = 0; b < l.x_bytes; ++b) add_digit_range(diff[b], x0, x1, 8 * b, (y1 - y0) * mult);
+    for (int b = 0; b < l.y_bytes; ++b) add_digit_range(diff[l.x_bytes + b], y0, y1, 8 * b, (x1 - x0) * mult);
+}
+
 // --- step 1: compaction -----------------------------------------------------
-__global__ void __launch_bounds__(kThreads) compact_kernel(const gs_splat *__restrict__ splats, int64_t n, SortWs ws) {
-    __shared__ uint32_t s_hist[kThreads / 32][4][kBins];  // per-warp digit histograms, 32 KB
+__global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__restrict__ splats, int64_t n, SortWs ws,
+                                                           TileKeyLayout tl) {
+    __shared__ uint32_t s_hist[kThreads / 32][4][kBins];  // per-warp depth digit histograms, 32 KB
+    __shared__ uint32_t s_tdiff[kMaxTilePasses][kBins + 1];
     __shared__ uint32_t scratch[33];
     __shared__ uint64_t scratch64[33];
     __shared__ uint32_t s_slot;
     for (int i = threadIdx.x; i < (kThreads / 32) * 4 * kBins; i += kThreads) (&s_hist[0][0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kMaxTilePasses * (kBins + 1); i += kThreads) (&s_tdiff[0][0])[i] = 0;
     const uint32_t blk = dynamic_block(&ws.hdr->tile_ctr[kCtrCompact], &s_slot);
     const int64_t base = (int64_t)blk * kSortTileItems + (int64_t)threadIdx.x * kIpt;  // 16 consecutive per thread
-    uint32_t depth[kIpt], tiles[kIpt];
+    // (depth, tiles, rect lo, rect hi): one 16-byte vector per record
+    uint4 r4[kIpt];
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const int64_t i = base + k;
-        tiles[k] = i < n ? splat_word(splats, (uint32_t)i, rec::kTiles) : 0u;
-        depth[k] = i < n ? splat_word(splats, (uint32_t)i, rec::kDepth) : 0u;
+        r4[k] = i < n ? __ldg(reinterpret_cast<const uint4 *>(splats + i) + 3) : make_uint4(0u, 0u, 0u, 0u);
     }
     uint32_t vis = 0;  // bit k: element base + k is visible
 #pragma unroll
-    for (int k = 0; k < kIpt; ++k) vis |= (tiles[k] != 0u ? 1u : 0u) << k;
+    for (int k = 0; k < kIpt; ++k) vis |= (r4[k].y != 0u ? 1u : 0u) << k;
     uint32_t total;
     const uint32_t ex = block_exclusive_scan((uint32_t)__popc(vis), scratch, &total);
     const uint64_t excl = prefix_from_aggregates(ws.scan_state[0], blk, total, ws.hdr, scratch64);
     uint32_t pos = (uint32_t)excl + ex;
     const unsigned warp = threadIdx.x >> 5;
+    const bool small_grid = tl.x_bytes == 1 && tl.y_bytes <= 1;
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
+        const uint32_t d = r4[k].x;
         if ((vis >> k) & 1u) {
-            const uint32_t d = depth[k], g = (uint32_t)(base + k);
+            const uint32_t g = (uint32_t)(base + k);
             ws.dkey[0][pos] = d;  // positive float: uint order = float order
             ws.dval[0][pos] = g;
             ws.depthv[g] = d;
+            ws.rectv[g] = make_uint2(r4[k].z, r4[k].w);
             ++pos;
             atomicAdd(&s_hist[warp][0][d & 0xffu], 1u);
             atomicAdd(&s_hist[warp][1][(d >> 8) & 0xffu], 1u);
+            const uint32_t x0 = r4[k].z & 0xffffu, y0 = r4[k].z >> 16, x1 = r4[k].w & 0xffffu, y1 = r4[k].w >> 16;
+            if (small_grid) {  // one byte per coordinate: digit = tx, then ty, no wrap
+                atomicAdd(&s_tdiff[0][x0], y1 - y0);
+                atomicSub(&s_tdiff[0][x1], y1 - y0);
+                if (tl.y_bytes) {
+                    atomicAdd(&s_tdiff[1][y0], x1 - x0);
+                    atomicSub(&s_tdiff[1][y1], x1 - x0);
+                }
+            } else {
+                add_rect_digits(s_tdiff, tl, x0, x1, y0, y1, 1u);
+            }
         }
         // the two high bytes take few distinct values: aggregate them per warp
-        warp_hist_add(s_hist[warp][2], ((vis >> k) & 1u) ? ((depth[k] >> 16) & 0xffu) : 0xffffffffu);
-        warp_hist_add(s_hist[warp][3], ((vis >> k) & 1u) ? (depth[k] >> 24) : 0xffffffffu);
+        warp_hist_add(s_hist[warp][2], ((vis >> k) & 1u) ? ((d >> 16) & 0xffu) : 0xffffffffu);
+        warp_hist_add(s_hist[warp][3], ((vis >> k) & 1u) ? (d >> 24) : 0xffffffffu);
     }
     if (blk == gridDim.x - 1 && threadIdx.x == 0) ws.hdr->nvis = (uint32_t)(excl + total);
     __syncthreads();
@@ -236,52 +290,53 @@ __global__ void __launch_bounds__(kThreads) compact_kernel(const gs_splat *__res
         for (int w = 0; w < kThreads / 32; ++w) c += s_hist[w][i / kBins][i % kBins];
         if (c) atomicAdd(&ws.hist_depth[i], c);
     }
+    for (int i = threadIdx.x; i < tl.passes * (kBins + 1); i += kThreads) {
+        const uint32_t c = (&s_tdiff[0][0])[i];
+        if (c) atomicAdd(&ws.hist_tile[i], c);  // differences add mod 2^32
+    }
 }
 
-// --- steps 2 and 5: one stable LSD radix pass -------------------------------
-// kFinal: write the full 64-bit key (tile << 32 | depth bits of the value).
-template <bool kFinal>
-__global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(const uint32_t *__restrict__ kin,
-                                                            const uint32_t *__restrict__ vin,
-                                                            uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                            uint64_t *__restrict__ kout64,
-                                                            const uint32_t *__restrict__ depthv,
-                                                            const uint32_t *__restrict__ count_ptr, int shift,
-                                                            const uint32_t *__restrict__ digit_total,
-                                                            uint64_t *__restrict__ state, uint32_t *__restrict__ ctr,
-                                                            SortHeader *__restrict__ hdr) {
-    __shared__ uint32_t s_keys[kSortTileItems];
-    __shared__ uint32_t s_vals[kSortTileItems];
-    __shared__ uint32_t s_wcnt[kThreads / 32][kBins];
-    __shared__ uint32_t s_base[kBins];
-    __shared__ uint32_t s_dstart[kBins];
-    __shared__ uint32_t scratch[33];
-    __shared__ uint32_t s_slot;
+// --- steps 2, 4 and 5: stable LSD radix passes -------------------------------
+// The ranking and scatter of one block of up to kSortTileItems elements, by
+// the 8-bit digit at `shift`.  Warp w holds elements [w*512, w*512 + 512) of
+// the block, lane-strided: key[k] is element w*512 + k*32 + lane.
+// digit_total: this thread's digit's count over all blocks.  val(k) gives
+// element k's value; it is asked for only after the look-back, so a caller
+// that loads values from memory keeps them out of registers while ranking.
+// kFinal: write the full 64-bit key (row-major tile id << 32 | depth bits of
+// the value), the tile id rebuilt from the byte-aligned key.
+template <int IPT>
+struct SweepSmemT {
+    uint32_t keys[IPT * kThreads];
+    uint32_t vals[IPT * kThreads];
+    uint32_t wcnt[kThreads / 32][kBins];
+    uint32_t base[kBins];
+    uint32_t dstart[kBins];
+    uint32_t scratch[33];
+};
+using SweepSmem = SweepSmemT<kIpt>;
 
-    const uint32_t n = *count_ptr;
-    const uint32_t nblocks = (n + kSortTileItems - 1) / kSortTileItems;
+template <bool kFinal, int IPT, typename ValFn>
+__device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t (&key)[IPT], ValFn val,
+                                             uint32_t start, uint32_t n, uint32_t blk, int shift,
+                                             uint32_t digit_total, uint64_t *__restrict__ state, SortHeader *hdr,
+                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                             uint64_t *__restrict__ kout64, const uint32_t *__restrict__ depthv,
+                                             int shift_y, uint32_t tiles_x) {
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s_wcnt[w][t] = 0;
-    const uint32_t blk = dynamic_block(ctr, &s_slot);  // contains __syncthreads
-    if (blk >= nblocks) return;                        // uniform over the block
-    const uint32_t start = blk * kSortTileItems;
-
-    // stable warp-local ranking; warp w owns elements [w*512, w*512 + 512)
-    uint32_t key[kIpt], rank[kIpt];
     const unsigned lt = lanemask_lt();
-    const uint32_t wbase = start + warp * (kIpt * 32) + lane;
+    const uint32_t wbase = start + warp * (IPT * 32) + lane;
+    // stable warp-local ranking (sm.wcnt is zero on entry)
+    uint32_t rank[IPT];
 #pragma unroll
-    for (int k = 0; k < kIpt; ++k) key[k] = (wbase + k * 32 < n) ? kin[wbase + k * 32] : 0u;
-#pragma unroll
-    for (int k = 0; k < kIpt; ++k) {
+    for (int k = 0; k < IPT; ++k) {
         const bool valid = wbase + k * 32 < n;
         const uint32_t d = valid ? ((key[k] >> shift) & 0xffu) : kBins;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t old = 0;
-        if (valid) old = s_wcnt[warp][d];
+        if (valid) old = sm.wcnt[warp][d];
         __syncwarp();
-        if (valid && (peers & lt) == 0) s_wcnt[warp][d] = old + (uint32_t)__popc(peers);
+        if (valid && (peers & lt) == 0) sm.wcnt[warp][d] = old + (uint32_t)__popc(peers);
         __syncwarp();
         rank[k] = old + (uint32_t)__popc(peers & lt);
     }
@@ -290,31 +345,32 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(const uint32_t *_
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) {
-        const uint32_t c = s_wcnt[w][t];
-        s_wcnt[w][t] = cnt;
+        const uint32_t c = sm.wcnt[w][t];
+        sm.wcnt[w][t] = cnt;
         cnt += c;
     }
     uint32_t tot;
-    s_dstart[t] = block_exclusive_scan(cnt, scratch, &tot);
-    const uint32_t dbase = block_exclusive_scan(digit_total[t], scratch, &tot);
+    sm.dstart[t] = block_exclusive_scan(cnt, sm.scratch, &tot);
+    const uint32_t dbase = block_exclusive_scan(digit_total, sm.scratch, &tot);
     const uint64_t excl = look_back<8>(state + t, blk, kBins, cnt, hdr);
-    s_base[t] = dbase + (uint32_t)excl;
+    sm.base[t] = dbase + (uint32_t)excl;
     __syncthreads();
-    uint32_t vals[kIpt];
+    uint32_t vals[IPT];
 #pragma unroll
-    for (int k = 0; k < kIpt; ++k) vals[k] = (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u;
+    for (int k = 0; k < IPT; ++k) vals[k] = val(k);
+    __syncthreads();  // val() may read shared memory that the scatter below overwrites
 #pragma unroll
-    for (int k = 0; k < kIpt; ++k) {
+    for (int k = 0; k < IPT; ++k) {
         if (wbase + k * 32 < n) {
             const uint32_t d = (key[k] >> shift) & 0xffu;
-            const uint32_t pos = s_dstart[d] + s_wcnt[warp][d] + rank[k];
-            s_keys[pos] = key[k];
-            s_vals[pos] = vals[k];
+            const uint32_t pos = sm.dstart[d] + sm.wcnt[warp][d] + rank[k];
+            sm.keys[pos] = key[k];
+            sm.vals[pos] = vals[k];
         }
     }
     __syncthreads();
-    const uint32_t cnt_blk = min((uint32_t)kSortTileItems, n - start);
-    constexpr int kHalf = kIpt / 2;
+    const uint32_t cnt_blk = min((uint32_t)(IPT * kThreads), n - start);
+    constexpr int kHalf = IPT / 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t gp[kHalf], kk[kHalf], vv[kHalf];
@@ -324,10 +380,10 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(const uint32_t *_
             gp[k] = 0xffffffffu;
             kk[k] = vv[k] = 0u;
             if (j < cnt_blk) {
-                kk[k] = s_keys[j];
-                vv[k] = s_vals[j];
+                kk[k] = sm.keys[j];
+                vv[k] = sm.vals[j];
                 const uint32_t d = (kk[k] >> shift) & 0xffu;
-                gp[k] = s_base[d] + (j - s_dstart[d]);
+                gp[k] = sm.base[d] + (j - sm.dstart[d]);
             }
         }
         if (kFinal) {
@@ -337,7 +393,8 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(const uint32_t *_
 #pragma unroll
             for (int k = 0; k < kHalf; ++k)
                 if (gp[k] < n) {  // false only for idle slots (or inconsistent digit totals)
-                    kout64[gp[k]] = ((uint64_t)kk[k] << 32) | dv[k];
+                    const uint32_t tile = (kk[k] >> shift_y) * tiles_x + (kk[k] & ((1u << shift_y) - 1u));
+                    kout64[gp[k]] = ((uint64_t)tile << 32) | dv[k];
                     vout[gp[k]] = vv[k];
                 }
         } else {
@@ -351,9 +408,49 @@ __global__ void __launch_bounds__(kThreads, 3) onesweep_kernel(const uint32_t *_
     }
 }
 
-// --- step 3: instance offsets in depth order ---------------------------------
-__global__ void __launch_bounds__(kThreads) offsets_kernel(const gs_splat *__restrict__ splats, SortWs ws,
-                                                           uint64_t m_cap) {
+// One pass over (key, value) arrays in device memory, IPT x 256 elements per
+// block.  diff_hist: the digit totals are given as a difference array (the
+// tile passes).
+template <bool kFinal, int IPT>
+__global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(const uint32_t *__restrict__ kin,
+                                                            const uint32_t *__restrict__ vin,
+                                                            uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                            uint64_t *__restrict__ kout64,
+                                                            const uint32_t *__restrict__ depthv,
+                                                            const uint32_t *__restrict__ count_ptr, int shift,
+                                                            const uint32_t *__restrict__ digit_total, bool diff_hist,
+                                                            uint64_t *__restrict__ state, uint32_t *__restrict__ ctr,
+                                                            SortHeader *__restrict__ hdr, int shift_y,
+                                                            uint32_t tiles_x) {
+    __shared__ SweepSmemT<IPT> sm;
+    __shared__ uint32_t s_slot;
+    const uint32_t n = *count_ptr;
+    const uint32_t nblocks = (n + IPT * kThreads - 1) / (IPT * kThreads);
+    const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) sm.wcnt[w][t] = 0;
+    const uint32_t blk = dynamic_block(ctr, &s_slot);  // contains __syncthreads
+    if (blk >= nblocks) return;                        // uniform over the block
+    const uint32_t start = blk * (IPT * kThreads);
+    const uint32_t wbase = start + warp * (IPT * 32) + lane;
+    uint32_t key[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) key[k] = (wbase + k * 32 < n) ? kin[wbase + k * 32] : 0u;
+    uint32_t dt = digit_total[t];
+    if (diff_hist) {  // uniform
+        uint32_t tot;
+        dt += block_exclusive_scan(dt, sm.scratch, &tot);
+    }
+    auto val = [&](int k) { return (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u; };
+    rank_scatter<kFinal>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv, shift_y,
+                         tiles_x);
+}
+
+// --- step 3: instance offsets in depth order -----------------------------------
+// Also, if the instances overflow the caller's capacity, takes the dropped
+// ones (global index >= m_cap) out of the tile digit counts, so that the
+// counts match the instances the tile passes sort.
+__global__ void __launch_bounds__(kThreads) offsets_kernel(SortWs ws, uint64_t m_cap, TileKeyLayout tl) {
     __shared__ uint64_t scratch[33];
     __shared__ uint32_t s_slot;
     const uint32_t n = ws.hdr->nvis;
@@ -366,22 +463,33 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(const gs_splat *__res
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const uint32_t i = base + k;
-        tt[k] = i < n ? splat_word(splats, ws.dval[0][i], rec::kTiles) : 0u;
+        const uint2 rc = i < n ? ws.rectv[ws.dval[0][i]] : make_uint2(0u, 0u);
+        tt[k] = ((rc.y & 0xffffu) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.x >> 16));
         sum += tt[k];
     }
     uint64_t total;
     const uint64_t ex = block_exclusive_scan64(sum, scratch, &total);
     const uint64_t excl = prefix_from_aggregates(ws.scan_state[1], blk, total, ws.hdr, scratch);
     uint64_t pos = excl + ex;
-    const uint64_t ndup = (m_cap + kDupItems - 1) / kDupItems;
+    const uint64_t nsweep = (m_cap + kSortTileItems - 1) / kSortTileItems;
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const uint32_t i = base + k;
         if (i < n) {
             ws.offs[i] = (uint32_t)(pos < 0xffffffffull ? pos : 0xffffffffull);
-            // duplicate blocks whose first instance falls inside this splat's run
-            for (uint64_t b = (pos + kDupItems - 1) / kDupItems; b * kDupItems < pos + tt[k] && b <= ndup; ++b)
+            // tile-pass blocks whose first instance falls inside this splat's run
+            for (uint64_t b = (pos + kSortTileItems - 1) / kSortTileItems;
+                 b * kSortTileItems < pos + tt[k] && b <= nsweep; ++b)
                 ws.dup_start[b] = i;
+            if (pos + tt[k] > m_cap) {  // overflow: uncount the dropped instances
+                const uint2 rc = ws.rectv[ws.dval[0][i]];
+                const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
+                const uint32_t kept = pos >= m_cap ? 0u : (uint32_t)(m_cap - pos);
+                const uint32_t w = x1 - x0, rows = kept / w, part = kept % w;
+                uint32_t(*diff)[kBins + 1] = reinterpret_cast<uint32_t(*)[kBins + 1]>(ws.hist_tile);
+                add_rect_digits(diff, tl, x0, x1, y0 + rows + 1u, y1, 0xffffffffu);        // whole rows
+                add_rect_digits(diff, tl, x0 + part, x1, y0 + rows, y0 + rows + 1u, 0xffffffffu);  // a partial row
+            }
         }
         pos += tt[k];
     }
@@ -393,67 +501,114 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(const gs_splat *__res
     }
 }
 
-// --- step 4: duplicate, balanced by instance ---------------------------------
-__global__ void __launch_bounds__(kThreads) duplicate_kernel(const gs_splat *__restrict__ splats, SortWs ws,
-                                                             int tiles_x, int passes, uint32_t *__restrict__ okey,
-                                                             uint32_t *__restrict__ oval) {
-    __shared__ uint32_t s_off[kDupItems + 2];
-    __shared__ uint32_t s_rect[kDupItems + 1];  // x0 | y0 << 16
-    __shared__ uint32_t s_w[kDupItems + 1];     // rectangle width in tiles
-    __shared__ uint32_t s_gid[kDupItems + 1];
-    __shared__ uint32_t s_hist[kMaxTilePasses][kBins];
+// --- step 4 fused with the first tile pass ------------------------------------
+// Block b generates instances [b * 4096, b * 4096 + 4096) in (depth, id,
+// row-major tile) order -- each warp finds its instances' splats by a
+// running max over the splat starts, not by a search -- and ranks them by
+// the low byte of tx straight away, so the instances are written once,
+// already partitioned.
+struct GenSmem {
+    uint32_t off[kSortTileItems + 2];   // first instance of each splat of the block
+    uint32_t rect[kSortTileItems + 1];  // x0 | y0 << 16
+    uint32_t gid[kSortTileItems + 1];
+    uint16_t w[kSortTileItems + 2];     // rectangle width in tiles (< 2^16)
+    uint16_t mark[kSortTileItems];      // block-local splat starting at each instance, else 0
+};
+
+template <bool kFinal>
+__global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileKeyLayout tl, uint32_t tiles_x,
+                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                             uint64_t *__restrict__ kout64) {
+    __shared__ union {
+        GenSmem gen;
+        SweepSmem sweep;
+    } sm;
+    __shared__ uint32_t s_slot;
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_wmax[kThreads / 32];
     const uint32_t m = ws.hdr->m_sort, nvis = ws.hdr->nvis;
     const uint64_t m_total = ws.hdr->m_total;
-    const uint32_t q0 = blockIdx.x * kDupItems;
-    if (q0 >= m) return;  // uniform
-    const uint32_t q1 = min(q0 + (uint32_t)kDupItems, m);
-    for (int i = threadIdx.x; i < kMaxTilePasses * kBins; i += kThreads) (&s_hist[0][0])[i] = 0;
+    const uint32_t nblocks = (m + kSortTileItems - 1) / kSortTileItems;
+    const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    const uint32_t blk = dynamic_block(&ws.hdr->tile_ctr[kCtrTiles], &s_slot);  // contains __syncthreads
+    if (blk >= nblocks) return;  // uniform
+    const uint32_t q0 = blk * kSortTileItems;
+    const uint32_t q1 = min(q0 + (uint32_t)kSortTileItems, m);
     // splats from the one holding q0 to the one holding the next block's first
-    // instance (at most kDupItems + 1: every splat has >= 1 instance)
-    const uint32_t s_lo = ws.dup_start[blockIdx.x];
-    const uint32_t s_hi = ((uint64_t)q1 < m_total && q1 == q0 + (uint32_t)kDupItems) ? ws.dup_start[blockIdx.x + 1]
-                                                                                      : nvis - 1;
-    const uint32_t plo = s_lo, cnt = min(s_hi - s_lo + 1, (uint32_t)kDupItems + 1);
-    for (uint32_t j = threadIdx.x; j < cnt; j += kThreads) {
-        const uint32_t p = plo + j;
+    // instance (at most kSortTileItems + 1: every splat has >= 1 instance)
+    const uint32_t s_lo = ws.dup_start[blk];
+    const uint32_t s_hi = ((uint64_t)q1 < m_total && q1 == q0 + (uint32_t)kSortTileItems) ? ws.dup_start[blk + 1]
+                                                                                           : nvis - 1;
+    const uint32_t cnt = min(s_hi - s_lo + 1, (uint32_t)kSortTileItems + 1);
+    for (uint32_t p = t; p < kSortTileItems; p += kThreads) sm.gen.mark[p] = 0;
+    for (uint32_t j = t; j < cnt; j += kThreads) {
+        const uint32_t p = s_lo + j;
         const uint32_t g = ws.dval[0][p];
-        const uint32_t lo = splat_word(splats, g, rec::kRectLo), hi = splat_word(splats, g, rec::kRectHi);
-        s_off[j] = ws.offs[p];
-        s_rect[j] = lo;
-        s_w[j] = (hi & 0xffffu) - (lo & 0xffffu);
-        s_gid[j] = g;
-    }
-    if (threadIdx.x == 0) {
-        const uint32_t p = plo + cnt;
-        s_off[cnt] = p < nvis ? ws.offs[p] : (uint32_t)(m_total < 0xffffffffull ? m_total : 0xffffffffull);
+        const uint2 rc = ws.rectv[g];
+        sm.gen.off[j] = ws.offs[p];
+        sm.gen.rect[j] = rc.x;
+        sm.gen.w[j] = (uint16_t)((rc.y & 0xffffu) - (rc.x & 0xffffu));
+        sm.gen.gid[j] = g;
     }
     __syncthreads();
-#pragma unroll 2
-    for (int k = 0; k < kDupItems / kThreads; ++k) {
-        const uint32_t q = q0 + (uint32_t)(k * kThreads) + threadIdx.x;
-        uint32_t tile = 0xffffffffu;
-        if (q < q1) {
-            uint32_t lo = 0, hi = cnt;  // s_off[lo] <= q < s_off[hi]
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_off[mid] <= q) lo = mid; else hi = mid;
-            }
-            const uint32_t local = q - s_off[lo];
-            const uint32_t w = s_w[lo], r = s_rect[lo];
-            const uint32_t ty = (r >> 16) + local / w;
-            const uint32_t tx = (r & 0xffffu) + local % w;
-            tile = ty * (uint32_t)tiles_x + tx;
-            okey[q] = tile;
-            oval[q] = s_gid[lo];
+    for (uint32_t j = 1 + t; j < cnt; j += kThreads) {
+        const uint32_t o = sm.gen.off[j];
+        if (o >= q0 && o - q0 < (uint32_t)kSortTileItems) sm.gen.mark[o - q0] = (uint16_t)j;
+    }
+    __syncthreads();
+    // splat of each position = running max of the marks, in the warp layout
+    // (position w*512 + k*32 + lane): a warp scan per k, carried across k,
+    // then across warps
+    const uint32_t pw = warp * (kIpt * 32) + lane;  // this thread's first position
+    uint32_t js[kIpt];
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) {
+        uint32_t v = sm.gen.mark[pw + k * 32];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= (unsigned)o) v = max(v, x);
         }
-        for (int p = 0; p < passes; ++p)
-            warp_hist_add(s_hist[p], tile == 0xffffffffu ? 0xffffffffu : ((tile >> (8 * p)) & 0xffu));
+        v = max(v, carry);
+        carry = __shfl_sync(0xffffffffu, v, 31);
+        js[k] = v;
     }
+    if (lane == 0) s_wmax[warp] = carry;
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kBins; i += kThreads) {
-        const uint32_t c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&ws.hist_tile[i], c);
+    uint32_t prev = 0;
+    for (unsigned w = 0; w < warp; ++w) prev = max(prev, s_wmax[w]);
+    uint32_t key[kIpt], val[kIpt];
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) {
+        const uint32_t p = pw + k * 32;
+        key[k] = val[k] = 0u;
+        if (q0 + p < q1) {
+            const uint32_t j = max(js[k], prev);
+            const uint32_t local = q0 + p - sm.gen.off[j];
+            const uint32_t w = sm.gen.w[j], r = sm.gen.rect[j];
+            // row = local / w by a float estimate and an exact integer correction
+            uint32_t row = (uint32_t)((float)local * __frcp_rn((float)w));
+            int64_t rem = (int64_t)local - (int64_t)row * w;
+            while (rem < 0) { --row; rem += w; }
+            while (rem >= (int64_t)w) { ++row; rem -= w; }
+            key[k] = (((r >> 16) + row) << tl.shift_y) | ((r & 0xffffu) + (uint32_t)rem);
+            val[k] = sm.gen.gid[j];
+        }
     }
+    // pass-0 digit counts from their difference array
+    uint32_t tot;
+    const uint32_t diff = ws.hist_tile[t];
+    const uint32_t digit_total = block_exclusive_scan(diff, s_scan, &tot) + diff;  // ends with a barrier:
+    // generation smem is dead.  Park the values where the sweep's value
+    // array lives (read back after its look-back) and free the registers.
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) sm.sweep.vals[pw + k * 32] = val[k];
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
+    __syncthreads();
+    rank_scatter<kFinal>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+                         ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
 }
 
 // --- step 6: ranges ----------------------------------------------------------
@@ -478,17 +633,20 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, const SortHeade
 }  // namespace
 
 // Steps 1-3 (through M).
-cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, cudaStream_t st) {
+cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
+                              uint32_t num_tiles, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(ws.hdr, 0, ws.zero_bytes, st);
     if (e != cudaSuccess || n == 0) return e;
+    const TileKeyLayout tl = tile_key_layout((uint32_t)tiles_x, num_tiles / (uint32_t)tiles_x);
     const uint32_t nb = (uint32_t)sort_blocks_for((uint64_t)n);
-    compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws);
+    compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
+    const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
     for (int p = 0; p < 4; ++p)
-        onesweep_kernel<false><<<nb, kThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+        onesweep_kernel<false, kDepthIpt><<<nbd, kThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
-                                                         ws.hist_depth + kBins * p, ws.depth_state[p],
-                                                         &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr);
-    offsets_kernel<<<nb, kThreads, 0, st>>>(splats, ws, m_cap);
+                                                         ws.hist_depth + kBins * p, false, ws.depth_state[p],
+                                                         &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
+    offsets_kernel<<<nb, kThreads, 0, st>>>(ws, m_cap, tl);
     return cudaGetLastError();
 }
 
@@ -497,23 +655,30 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
 // reads the workspace and writes the caller's keys and values.
 cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
                              uint32_t num_tiles, uint64_t *keys, uint32_t *vals, uint32_t *ranges, cudaStream_t st) {
+    (void)splats;
     if (n > 0 && m_cap > 0) {
-        const int passes = tile_passes_of(num_tiles);
+        const TileKeyLayout tl = tile_key_layout((uint32_t)tiles_x, num_tiles / (uint32_t)tiles_x);
+        const int passes = tl.passes;
         uint32_t *scratch_k = reinterpret_cast<uint32_t *>(keys), *scratch_v = scratch_k + m_cap;
         auto buf_k = [&](int k) { return ((passes - 1 - k) % 2 == 0) ? ws.tkey : scratch_k; };
         auto buf_v = [&](int k) { return ((passes - 1 - k) % 2 == 0) ? ws.tval : scratch_v; };
-        const uint32_t nd = (uint32_t)((m_cap + kDupItems - 1) / kDupItems);
-        duplicate_kernel<<<nd, kThreads, 0, st>>>(splats, ws, tiles_x, passes, buf_k(0), buf_v(0));
         const uint32_t nb = (uint32_t)sort_blocks_for(m_cap);
-        for (int p = 0; p < passes; ++p) {
+        const uint32_t tx = (uint32_t)tiles_x;
+        if (passes == 1)
+            dup_sweep_kernel<true><<<nb, kThreads, 0, st>>>(ws, tl, tx, nullptr, vals, keys);
+        else
+            dup_sweep_kernel<false><<<nb, kThreads, 0, st>>>(ws, tl, tx, buf_k(1), buf_v(1), nullptr);
+        for (int p = 1; p < passes; ++p) {
+            const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
             if (p == passes - 1)
-                onesweep_kernel<true><<<nb, kThreads, 0, st>>>(
-                    buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv, &ws.hdr->m_sort, 8 * p,
-                    ws.hist_tile + kBins * p, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr);
+                onesweep_kernel<true, kIpt><<<nb, kThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
+                                                                &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
+                                                                &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
+                                                                tx);
             else
-                onesweep_kernel<false><<<nb, kThreads, 0, st>>>(
-                    buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p,
-                    ws.hist_tile + kBins * p, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr);
+                onesweep_kernel<false, kIpt><<<nb, kThreads, 0, st>>>(
+                    buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
+                    true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }
     }
     ranges_kernel<<<(num_tiles + 255) / 256, 256, 0, st>>>(keys, ws.hdr, num_tiles, reinterpret_cast<uint2 *>(ranges));

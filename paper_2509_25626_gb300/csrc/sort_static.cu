@@ -8,7 +8,7 @@
 // a caller-provided workspace.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads
-// the library holds it (36 MiB) until the process exits.  Host code cannot
+// the library holds it (38 MiB) until the process exits.  Host code cannot
 // use the array's name as a device address, so the first call on each
 // device resolves the address with cudaGetSymbolAddress (with that device
 // current) and caches it; make that first call before any stream capture.
@@ -22,14 +22,15 @@
 
 namespace gs {
 
-cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, cudaStream_t st);
+cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
+                              uint32_t num_tiles, cudaStream_t st);
 cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
                              uint32_t num_tiles, uint64_t *keys, uint32_t *vals, uint32_t *ranges, cudaStream_t st);
 void set_cuda_error(cudaError_t e);
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = (size_t)36 << 20;  // >= carve_sort_ws(max n, max m_cap)
+constexpr size_t kStaticScratchBytes = (size_t)38 << 20;  // >= carve_sort_ws(max n, max m_cap)
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_sort_scratch[kStaticScratchBytes];
@@ -82,7 +83,7 @@ extern "C" int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera
     cudaStream_t st = (cudaStream_t)stream;
     SortWs ws;
     carve_sort_ws(static_cast<char *>(slot.ptr), n, m_cap, num_tiles, &ws);
-    e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, st);
+    e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, (int)tiles_x, (uint32_t)num_tiles, st);
     if (e == cudaSuccess && m_out) {
         SortHeader h;
         e = cudaMemcpyAsync(&h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, st);

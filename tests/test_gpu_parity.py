@@ -141,6 +141,35 @@ def test_end_to_end_parity(case, oracle_frames):
     print(name, "flipped", len(flipped), rep)
 
 
+@pytest.mark.parametrize("case", ["tiny_200x120", "clustered60k_orbit7"])
+def test_workload_counts_match_oracle(case, oracle_frames):
+    """gs_render_workload on the oracle's records: the image equals gs_render
+    bit for bit (same loop), n_eval (Gaussian-pixel evaluations) equals the
+    oracle's count on every pixel with no near decision, and every tile gets
+    a positive cycle count, larger on average for tiles with longer lists."""
+    name, sc, cam = next(c for c in SMALL if c[0] == case)
+    pre, srt, img = oracle_frames[name]
+    rec = to_dev_records(records_from_oracle(pre, SPLAT_DTYPE))
+    vals = torch.from_numpy(np.ascontiguousarray(srt["vals"]).view(np.int32).copy()).to(DEV)
+    ranges = torch.from_numpy(srt["ranges"].view(np.int32).copy()).to(DEV)
+    bg = (0.1, 0.2, 0.3)
+    out_w, T_w, nc_w, ne, cyc = gs.render_workload(rec, vals, ranges, cam, bg, tile_cycles=True)
+    out, T, nc = gs.render(rec, vals, ranges, cam, bg=bg)
+    torch.cuda.synchronize()
+    assert torch.equal(out_w, out) and torch.equal(T_w, T) and torch.equal(nc_w, nc)
+    exact = img["near"] == 0
+    ne = ne.cpu().numpy().astype(np.int64)
+    bad = (ne != img["n_eval"]) & exact
+    assert not np.any(bad), f"n_eval differs on {bad.sum()} pixels with no near decision"
+    cyc = cyc.cpu().numpy()
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    assert cyc.shape == (ty, tx) and np.all(cyc > 0)
+    rg = srt["ranges"].reshape(-1, 2).astype(np.int64)
+    lens = (rg[:, 1] - rg[:, 0]).reshape(ty, tx)
+    if np.any(lens == 0) and np.any(lens > 0):
+        assert cyc[lens > np.median(lens[lens > 0])].mean() > cyc[lens == 0].mean()
+
+
 def test_batches_stop_permanently(oracle):
     """A tile with 600 stacked splats that saturates in the first batch of
     256: the pixel must not resume in later batches (a failure mode the
@@ -204,6 +233,23 @@ def test_sh_degrees(oracle):
         compare_preprocess(gpu_records(sc, cam), pre, cam)
 
 
+@pytest.mark.parametrize("wh", [(4112, 40), (40, 4112), (4200, 4200)])
+def test_sort_wide_and_tall_images(oracle, wh):
+    """Tile grids wider or taller than 256 tiles: the byte-aligned tile key
+    takes 2 bytes for that coordinate (2, 3 and 4 radix passes here); keys,
+    values and ranges stay bit-exact on the oracle's records."""
+    w, h = wh
+    sc, cam = tiny_scene(4000, w + h, w, h, log_scale=(-3.0, 0.9) if min(w, h) < 100 else (-5.0, 0.6))
+    pre = oracle.preprocess(sc, cam)
+    srt = oracle.duplicate_sort(pre, cam)
+    rec = records_from_oracle(pre, SPLAT_DTYPE)
+    keys, vals, ranges, m, _, _ = gpu_sort(to_dev_records(rec), sc.n, cam)
+    assert m == srt["m"] and m > 0
+    assert np.array_equal(keys, srt["keys"])
+    assert np.array_equal(vals, srt["vals"])
+    assert np.array_equal(ranges, srt["ranges"])
+
+
 def test_capacity_overflow_reported():
     sc, cam = tiny_scene(2000, 4, 128, 96, log_scale=(-2.8, 0.6))
     st = SceneTensors.from_scene(sc, DEV)
@@ -219,6 +265,22 @@ def test_capacity_overflow_reported():
     assert m2 == m and over
     keys, vals, ranges, m3, ws = gs.sort(sp, sc.n, cam, m)  # exact fit
     assert m3 == m and gs.sort_status(ws) == (m, False)
+    # On overflow the output is still a sorted list of the first m_cap
+    # instances in generation (depth, id, row-major tile) order, so that a
+    # render of it reads only valid splats.
+    full_k = keys.cpu().numpy().view(np.uint64)[:m]
+    full_v = vals.cpu().numpy().view(np.uint32)[:m]
+    for cap in (m // 2 + 7, 1):
+        k2, v2, r2, _, ws2 = gs.sort(sp, sc.n, cam, cap, count=False)
+        torch.cuda.synchronize()
+        assert gs.sort_status(ws2) == (m, True)
+        tile, depth = full_k >> np.uint64(32), full_k & np.uint64(0xFFFFFFFF)
+        gen = np.lexsort((tile, full_v, depth))[:cap]  # generation order: depth, id, tile
+        kept = np.lexsort((full_v[gen], full_k[gen]))
+        assert np.array_equal(k2.cpu().numpy().view(np.uint64)[:cap], full_k[gen][kept])
+        assert np.array_equal(v2.cpu().numpy().view(np.uint32)[:cap], full_v[gen][kept])
+        gs.render(sp, v2, r2, cam)
+        torch.cuda.synchronize()
 
 
 def test_renderer_no_sync_matches_stepwise():

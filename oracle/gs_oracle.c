@@ -354,6 +354,9 @@ void oracle_duplicate_sort(int64_t n, const int32_t *rect, const int32_t *tiles,
  *
  * ids[0..len) is the pixel's front-to-back list.  Besides the colour, final
  * T and contributor index, it reports:
+ *   invdepth      the inverse depth blended like a colour channel, without
+ *                 background: sum over blended Gaussians of alpha T / z (the
+ *                 optional output of the paper's render kernels, Appendix B)
  *   n_eval        Gaussians evaluated before the pixel stopped (the
  *                 "Gaussian-pixel evaluations" work count)
  *   near_count    decisions whose log-space margin is under tau, widened by
@@ -364,6 +367,7 @@ void oracle_duplicate_sort(int64_t n, const int32_t *rect, const int32_t *tiles,
  * ------------------------------------------------------------------------- */
 typedef struct {
     double color[3];
+    double invdepth;
     double T;
     int32_t n_contrib;
     int32_t n_eval;
@@ -372,10 +376,10 @@ typedef struct {
 } pixel_t;
 
 static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int64_t len, const double *xy,
-                               const double *conic, const double *opacity, const double *rgb, const double *bg,
-                               double tau_alpha, double tau_T, double pos_eps, double cmax) {
+                               const double *conic, const double *opacity, const double *rgb, const double *depth,
+                               const double *bg, double tau_alpha, double tau_T, double pos_eps, double cmax) {
     pixel_t out;
-    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0;
     int32_t contrib = 0, last = 0, near = 0;
     double impact = 0.0;
     double bgmax = fmax(bg[0], fmax(bg[1], bg[2]));
@@ -404,10 +408,12 @@ static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int6
         }
         if (Tn < T_MIN) break; /* stop; this Gaussian is not blended */
         for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * alpha * T;
+        D += alpha * T / depth[g];
         T = Tn;
         last = contrib;
     }
     for (int ch = 0; ch < 3; ++ch) out.color[ch] = C[ch] + T * bg[ch];
+    out.invdepth = D;
     out.T = T;
     out.n_contrib = last;
     out.n_eval = contrib;
@@ -422,9 +428,11 @@ static double max_rgb(int64_t n, const double *rgb) {
     return c;
 }
 
-static void store_pixel(const pixel_t *p, int64_t pix, int64_t npix, double *out_color, double *final_T,
-                        int32_t *n_contrib, int32_t *n_eval, int32_t *near_count, double *flip_impact) {
+static void store_pixel(const pixel_t *p, int64_t pix, int64_t npix, double *out_color, double *invdepth,
+                        double *final_T, int32_t *n_contrib, int32_t *n_eval, int32_t *near_count,
+                        double *flip_impact) {
     for (int ch = 0; ch < 3; ++ch) out_color[ch * npix + pix] = p->color[ch];
+    invdepth[pix] = p->invdepth;
     final_T[pix] = p->T;
     n_contrib[pix] = p->n_contrib;
     n_eval[pix] = p->n_eval;
@@ -437,9 +445,9 @@ static void store_pixel(const pixel_t *p, int64_t pix, int64_t npix, double *out
  * nthreads OpenMP threads if built with OpenMP. */
 void oracle_render(int width, int height, int row0, int row1, const uint32_t *ranges, const uint32_t *vals,
                    int64_t n, const double *xy, const double *conic, const double *opacity, const double *rgb,
-                   const double *bg, double tau_alpha, double tau_T, double pos_eps, int nthreads, double *out_color,
-                   double *final_T, int32_t *n_contrib, int32_t *n_eval, int32_t *near_count,
-                   double *flip_impact) {
+                   const double *depth, const double *bg, double tau_alpha, double tau_T, double pos_eps,
+                   int nthreads, double *out_color, double *invdepth, double *final_T, int32_t *n_contrib,
+                   int32_t *n_eval, int32_t *near_count, double *flip_impact) {
     int tiles_x = (width + TILE - 1) / TILE;
     int64_t npix = (int64_t)width * height;
     double cmax = max_rgb(n, rgb);
@@ -452,9 +460,9 @@ void oracle_render(int width, int height, int row0, int row1, const uint32_t *ra
             int tile = (py / TILE) * tiles_x + px / TILE;
             uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
             pixel_t p = composite_pixel((double)px, (double)py, vals + s, (int64_t)e - (int64_t)s, xy, conic,
-                                        opacity, rgb, bg, tau_alpha, tau_T, pos_eps, cmax);
-            store_pixel(&p, (int64_t)py * width + px, npix, out_color, final_T, n_contrib, n_eval, near_count,
-                        flip_impact);
+                                        opacity, rgb, depth, bg, tau_alpha, tau_T, pos_eps, cmax);
+            store_pixel(&p, (int64_t)py * width + px, npix, out_color, invdepth, final_T, n_contrib, n_eval,
+                        near_count, flip_impact);
         }
     }
 }
@@ -474,9 +482,9 @@ static int bf_cmp(const void *pa, const void *pb) {
 
 void oracle_render_bruteforce(int width, int height, int64_t n, const int32_t *rect, const int32_t *radius,
                               const float *depth32, const double *xy, const double *conic, const double *opacity,
-                              const double *rgb, const double *bg, int use_rect, double *out_color,
-                              double *final_T, int32_t *n_contrib, int32_t *n_eval, int32_t *near_count,
-                              double *flip_impact) {
+                              const double *rgb, const double *depth, const double *bg, int use_rect,
+                              double *out_color, double *invdepth, double *final_T, int32_t *n_contrib,
+                              int32_t *n_eval, int32_t *near_count, double *flip_impact) {
     int64_t npix = (int64_t)width * height;
     double cmax = max_rgb(n, rgb);
     uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
@@ -494,10 +502,10 @@ void oracle_render_bruteforce(int width, int height, int64_t n, const int32_t *r
                 ids[len++] = (uint32_t)g;
             }
             qsort(ids, (size_t)len, sizeof(uint32_t), bf_cmp);
-            pixel_t p = composite_pixel((double)px, (double)py, ids, len, xy, conic, opacity, rgb, bg, 0.0, 0.0,
-                                        0.0, cmax);
-            store_pixel(&p, (int64_t)py * width + px, npix, out_color, final_T, n_contrib, n_eval, near_count,
-                        flip_impact);
+            pixel_t p = composite_pixel((double)px, (double)py, ids, len, xy, conic, opacity, rgb, depth, bg, 0.0,
+                                        0.0, 0.0, cmax);
+            store_pixel(&p, (int64_t)py * width + px, npix, out_color, invdepth, final_T, n_contrib, n_eval,
+                        near_count, flip_impact);
         }
     free(ids);
 }

@@ -56,9 +56,9 @@ def _load():
             lib.oracle_duplicate_sort.restype = None
             lib.oracle_duplicate_sort.argtypes = [i64, P, P, P, i32, i32, i64, P, P, P]
             lib.oracle_render.restype = None
-            lib.oracle_render.argtypes = [i32, i32, i32, i32, P, P, i64, P, P, P, P, P, f64, f64, f64, i32] + [P] * 6
+            lib.oracle_render.argtypes = [i32, i32, i32, i32, P, P, i64, P, P, P, P, P, P, f64, f64, f64, i32] + [P] * 7
             lib.oracle_render_bruteforce.restype = None
-            lib.oracle_render_bruteforce.argtypes = [i32, i32, i64, P, P, P, P, P, P, P, P, i32] + [P] * 6
+            lib.oracle_render_bruteforce.argtypes = [i32, i32, i64, P, P, P, P, P, P, P, P, P, i32] + [P] * 7
             lib.oracle_sh_basis.restype = f64
             lib.oracle_sh_basis.argtypes = [i32, i32, f64, f64, f64]
             lib.oracle_has_openmp.restype = i32
@@ -164,8 +164,12 @@ def duplicate_sort(pre: dict, cam) -> dict:
     return dict(keys=keys[:m], vals=vals[:m], ranges=ranges, m=m)
 
 
+_RENDER_KEYS = ("color", "invdepth", "final_T", "n_contrib", "n_eval", "near", "flip_impact")
+
+
 def _render_outputs(w: int, h: int) -> dict:
-    return dict(color=np.zeros((3, h, w)), final_T=np.zeros((h, w)), n_contrib=np.zeros((h, w), np.int32),
+    return dict(color=np.zeros((3, h, w)), invdepth=np.zeros((h, w)), final_T=np.zeros((h, w)),
+                n_contrib=np.zeros((h, w), np.int32),
                 n_eval=np.zeros((h, w), np.int32), near=np.zeros((h, w), np.int32),
                 flip_impact=np.zeros((h, w)))
 
@@ -185,9 +189,8 @@ def render(pre: dict, srt: dict, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0
     vals = np.ascontiguousarray(srt["vals"] if srt["m"] else np.zeros(1, np.uint32))
     n = pre["xy"].shape[0]
     lib.oracle_render(w, h, r0, r1, _p(np.ascontiguousarray(srt["ranges"])), _p(vals), n, _p(pre["xy"]),
-                      _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(bgv), tau_alpha, tau_T,
-                      float(pos_eps), int(threads), *[_p(out[k]) for k in ("color", "final_T", "n_contrib", "n_eval", "near",
-                                                            "flip_impact")])
+                      _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]), _p(bgv), tau_alpha,
+                      tau_T, float(pos_eps), int(threads), *[_p(out[k]) for k in _RENDER_KEYS])
     return out
 
 
@@ -199,9 +202,8 @@ def render_bruteforce(pre: dict, cam, bg=(0.0, 0.0, 0.0), use_rect: bool = True)
     bgv = np.ascontiguousarray(bg, np.float64)
     n = pre["xy"].shape[0]
     lib.oracle_render_bruteforce(w, h, n, _p(pre["rect"]), _p(pre["radius"]), _p(pre["depth32"]),
-                                 _p(pre["xy"]), _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(bgv),
-                                 int(use_rect), *[_p(out[k]) for k in ("color", "final_T", "n_contrib", "n_eval",
-                                                                       "near", "flip_impact")])
+                                 _p(pre["xy"]), _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]),
+                                 _p(pre["depth"]), _p(bgv), int(use_rect), *[_p(out[k]) for k in _RENDER_KEYS])
     return out
 
 

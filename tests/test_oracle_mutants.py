@@ -25,6 +25,8 @@ MUTANTS = {
     "colour_offset": ("fmax(acc + 0.5, 0.0)", "fmax(acc, 0.0)"),
     "sh_index": ("Y[l * l + l + mm]", "Y[l * l + l - mm]"),
     "stop_not_permanent": ("if (Tn < T_MIN) break;", "if (Tn < T_MIN) continue;"),
+    "invdepth_weight_without_T": ("D += alpha * T / depth[g];", "D += alpha / depth[g];"),
+    "invdepth_depth_not_inverted": ("D += alpha * T / depth[g];", "D += alpha * T * depth[g];"),
     "n_contrib_blended_only": ("last = contrib;", "last = contrib - (contrib > 1);"),
     "rect_max_bound": ("floor((px + r + TILE - 1) / TILE)", "floor((px + r + TILE) / TILE)"),
     "range_end_off_by_one": ("ranges[2 * tile + 1] = (uint32_t)(i + 1);", "ranges[2 * tile + 1] = (uint32_t)i;"),

@@ -442,6 +442,54 @@ def test_white_splats_out_equals_one_minus_T(oracle):
     assert (img["final_T"] < 0.01).mean() > 0.05  # the scene does saturate
 
 
+def test_invdepth_single_gaussian_closed_form(oracle):
+    """One Gaussian at depth z: inverse depth = alpha / z on every pixel it
+    is blended on (alpha from the isotropic closed form), 0 elsewhere, and no
+    background term."""
+    cam = pinhole_camera(33, 33)
+    log_s, z, logit = -4.0, 3.0, 0.4
+    sc = one_scene([[0, 0, z]], [[log_s] * 3], [[1, 0, 0, 0]], [logit], [[dc_for_rgb(0.5)] * 3])
+    pre, srt, img = oracle.frame(sc, cam, bg=(0.3, 0.3, 0.3))
+    s = math.exp(float(np.float32(log_s)))
+    var = (f32(cam.fx) * s / z) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-float(np.float32(logit))))
+    zf = float(np.float32(z))  # the mean is stored in FP32
+    for py in range(33):
+        for px in range(33):
+            a = min(0.99, o * math.exp(-((px - 16) ** 2 + (py - 16) ** 2) / (2 * var)))
+            if a < 1 / 255:
+                a = 0.0
+            assert abs(img["invdepth"][py, px] - a / zf) < 1e-12
+
+
+def test_invdepth_equal_depths_telescopes(oracle):
+    """Gaussians all at one depth z0 (a fronto-parallel layer): the weights
+    alpha_i T_i telescope, so inverse depth = (1 - T_final) / z0, whatever the
+    skips and stops."""
+    rng = np.random.default_rng(4)
+    n, z0 = 400, 2.5
+    cam = pinhole_camera(64, 48)
+    xy = rng.uniform(-0.6, 0.6, size=(n, 2)) * np.array([cam.tan_fovx, cam.tan_fovy]) * z0
+    means = np.column_stack([xy, np.full(n, z0)])
+    sc = one_scene(means.tolist(), rng.normal(-3.0, 0.5, size=(n, 3)).tolist(), [[1, 0, 0, 0]] * n,
+                   rng.normal(0.0, 2.0, size=n).tolist(), [[dc_for_rgb(0.5)] * 3] * n)
+    pre, srt, img = oracle.frame(sc, cam)
+    assert (img["final_T"] < 0.05).mean() > 0.05 and img["n_contrib"].max() > 5
+    np.testing.assert_allclose(img["invdepth"], (1 - img["final_T"]) / float(np.float32(z0)), atol=1e-12)
+
+
+def test_invdepth_two_layers_by_hand(oracle):
+    """Two coaxial Gaussians at z1 < z2 seen at the principal point:
+    inverse depth = a1 / z1 + (1 - a1) a2 / z2."""
+    cam = pinhole_camera(33, 33)
+    z1, z2, o1, o2 = 2.0, 5.0, 0.6, 0.7
+    sc = one_scene([[0, 0, z1], [0, 0, z2]], [[-3.0] * 3] * 2, [[1, 0, 0, 0]] * 2,
+                   [math.log(o1 / (1 - o1)), math.log(o2 / (1 - o2))], [[dc_for_rgb(0.5)] * 3] * 2)
+    pre, srt, img = oracle.frame(sc, cam)
+    a1, a2 = pre["opacity"]  # alpha = opacity at the centre pixel (power = 0)
+    assert abs(centre(img, "invdepth") - (a1 / z1 + (1 - a1) * a2 / z2)) < 1e-12
+
+
 def test_background_enters_as_T_bg(oracle):
     sc, cam = tiny_scene(300, 8, 40, 40)
     bg = (0.25, 0.5, 1.0)

@@ -29,13 +29,17 @@ struct __align__(16) StagedB { float w11, lg2o, r, g; };
 
 struct Pixel {
     float T, c0, c1, c2;
+    float id;       // inverse depth accumulated like a colour channel (kDepth only)
     uint32_t last;  // 1-based list position of the last blended splat
     uint32_t stop;  // list position of the splat that stopped the pixel, 0 if none
     bool done;
 };
 
-__device__ __forceinline__ void blend(Pixel &p, float alpha, float r, float g, float b, uint32_t idx) {
-    if (p.done || alpha < kAlphaMin) return;
+// keep: alpha >= 1/255 (decided by the caller on log2 alpha); iz = 1 / depth
+template <bool kDepth>
+__device__ __forceinline__ void blend(Pixel &p, bool keep, float alpha, float r, float g, float b, float iz,
+                                      uint32_t idx) {
+    if (p.done || !keep) return;
     const float Tn = p.T * (1.0f - alpha);
     if (Tn < kTStop) {  // stop without blending this splat
         p.done = true;
@@ -46,10 +50,14 @@ __device__ __forceinline__ void blend(Pixel &p, float alpha, float r, float g, f
     p.c0 = fmaf(r, w, p.c0);
     p.c1 = fmaf(g, w, p.c1);
     p.c2 = fmaf(b, w, p.c2);
+    if (kDepth) p.id = fmaf(iz, w, p.id);
     p.T = Tn;
     p.last = idx;
 }
 
+// kDepth: also write, per pixel, the inverse depth blended like a colour
+// channel (no background term): sum of alpha T / depth over the blended
+// splats, the optional output of the paper's kernels (Appendix B).
 // kCount: also write, per pixel, how many splats were evaluated before the
 // pixel stopped (the stopping one included; the whole list if it never
 // stopped) -- the work measure of the paper's workload characterisation
@@ -63,6 +71,7 @@ struct RenderSmem {
     float c[kBatch];
     uint8_t mask[kBatch];
     uint8_t list[kWarps][kBatch];
+    float iz[kBatch];  // 1 / depth (kDepth only)
 };
 
 // Renders one tile with the whole block.  Every thread must call it; it
@@ -70,9 +79,10 @@ struct RenderSmem {
 // reused for the next tile.  The job's pointers and sizes are read where
 // they are used, not held in registers: the batch kernel keeps its job in
 // shared memory, the single-image kernel in its parameters.
-template <bool kCount>
+template <bool kCount, bool kDepth>
 __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job &job, const uint2 range, int tile,
-                                            uint32_t *__restrict__ n_eval, uint32_t *__restrict__ tile_cycles) {
+                                            float *__restrict__ invdepth, uint32_t *__restrict__ n_eval,
+                                            uint32_t *__restrict__ tile_cycles) {
     long long t_start = 0;
     if (kCount) t_start = clock64();
     const int width = job.width, tiles_x = (width + kTile - 1) / kTile;
@@ -88,8 +98,8 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
     const int px = bx0 + 2 * (int)(lane & 3u), py = by0 + (int)(lane >> 2);
     const float pxf = (float)px, pyf = (float)py;
     const bool in0 = px < width && py < job.height, in1 = px + 1 < width && py < job.height;
-    Pixel p0{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in0};
-    Pixel p1{1.f, 0.f, 0.f, 0.f, 0u, 0u, !in1};
+    Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !in0};
+    Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !in1};
 
     // corners of the tile, for the per-warp culling masks
     const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
@@ -110,6 +120,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
                 s_a[k] = StagedA{a.x, a.y, a.z, a.w};
                 s_b[k] = StagedB{b.x, b.y, b.z, b.w};
                 s_c[k] = c.x;
+                if (kDepth) sm.iz[k] = __frcp_rn(__ldg(reinterpret_cast<const float *>(src + 3)));
                 // box [x - hx, x + hx] x [y - hy, y + hy] against the 8x8 blocks
                 const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
                 const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
@@ -135,24 +146,30 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
         __syncwarp();
 
         const uint32_t pos0 = base - range.x + 1;  // list position of staged splat 0
-        for (uint32_t q = 0; q < cnt; ++q) {
-            if ((q & 7u) == 0u && __all_sync(0xffffffffu, p0.done && p1.done)) break;
-            const uint32_t j = s_list[warp][q];
-            const StagedA sa = s_a[j];
-            const StagedB sb = s_b[j];
-            const float dy = sa.y - pyf;
-            const float dx = sa.x - pxf;
-            const float t = sa.w01 * dy;
-            const float u0 = fmaf(sa.w00, dx, t);
-            const float u1 = u0 - sa.w00;  // dx - 1 for the right-hand pixel
-            const float v = sb.w11 * dy;
-            const float vv = fmaf(-v, v, sb.lg2o);
-            const float a0 = fminf(kAlphaMax, ex2_approx(fmaf(-u0, u0, vv)));
-            const float a1 = fminf(kAlphaMax, ex2_approx(fmaf(-u1, u1, vv)));
-            if (a0 >= kAlphaMin || a1 >= kAlphaMin) {
-                const float b = s_c[j];
-                blend(p0, a0, sb.r, sb.g, b, pos0 + j);
-                blend(p1, a1, sb.r, sb.g, b, pos0 + j);
+        for (uint32_t q8 = 0; q8 < cnt; q8 += 8) {
+            if (__all_sync(0xffffffffu, p0.done && p1.done)) break;  // warp-uniform
+            const uint32_t qe = min(cnt, q8 + 8u);
+#pragma unroll 2
+            for (uint32_t q = q8; q < qe; ++q) {
+                const uint32_t j = s_list[warp][q];
+                const StagedA sa = s_a[j];
+                const StagedB sb = s_b[j];
+                const float dy = sa.y - pyf;
+                const float dx = sa.x - pxf;
+                const float t = sa.w01 * dy;
+                const float u0 = fmaf(sa.w00, dx, t);
+                const float u1 = u0 - sa.w00;  // dx - 1 for the right-hand pixel
+                const float v = sb.w11 * dy;
+                const float vv = fmaf(-v, v, sb.lg2o);
+                const float e0 = fmaf(-u0, u0, vv), e1 = fmaf(-u1, u1, vv);  // log2 alpha before the clamp
+                // alpha >= 1/255 <=> log2 alpha >= -log2 255: decided before the exp
+                const bool k0 = e0 >= -kLog2_255, k1 = e1 >= -kLog2_255;
+                if (k0 || k1) {
+                    const float b = s_c[j];
+                    const float iz = kDepth ? sm.iz[j] : 0.f;
+                    blend<kDepth>(p0, k0, fminf(kAlphaMax, ex2_approx(e0)), sb.r, sb.g, b, iz, pos0 + j);
+                    blend<kDepth>(p1, k1, fminf(kAlphaMax, ex2_approx(e1)), sb.r, sb.g, b, iz, pos0 + j);
+                }
             }
         }
     }
@@ -169,6 +186,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
         job.final_T[pix] = p0.T;
         job.n_contrib[pix] = p0.last;
         if (kCount) n_eval[pix] = p0.stop ? p0.stop : len;
+        if (kDepth) invdepth[pix] = p0.id;
     }
     if (in1) {
         const size_t pix = (size_t)py * width + px + 1;
@@ -178,6 +196,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
         job.final_T[pix] = p1.T;
         job.n_contrib[pix] = p1.last;
         if (kCount) n_eval[pix] = p1.stop ? p1.stop : len;
+        if (kDepth) invdepth[pix] = p1.id;
     }
     __syncthreads();  // shared memory free for the next tile
     if (kCount && tile_cycles != nullptr && threadIdx.x == 0) {
@@ -186,14 +205,15 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
     }
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads) render_kernel(const gs_splat *__restrict__ splats,
+template <bool kCount, bool kDepth>
+__global__ void __launch_bounds__(kThreads, 10) render_kernel(const gs_splat *__restrict__ splats,
                                                           const uint32_t *__restrict__ vals,
                                                           const uint2 *__restrict__ ranges, int width, int height,
                                                           float bg_r, float bg_g, float bg_b,
                                                           float *__restrict__ out_color,
                                                           float *__restrict__ final_T,
                                                           uint32_t *__restrict__ n_contrib,
+                                                          float *__restrict__ invdepth,
                                                           uint32_t *__restrict__ n_eval,
                                                           uint32_t *__restrict__ tile_cycles) {
     __shared__ RenderSmem sm;
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const gs_splat *__rest
     job.bg[1] = bg_g;
     job.bg[2] = bg_b;
     job.tile_begin = 0;
-    render_tile<kCount>(sm, job, ranges[blockIdx.x], blockIdx.x, n_eval, tile_cycles);
+    render_tile<kCount, kDepth>(sm, job, ranges[blockIdx.x], blockIdx.x, invdepth, n_eval, tile_cycles);
 }
 
 // Persistent render of many jobs (requests): blocks pull work items -- one
@@ -244,7 +264,8 @@ __global__ void __launch_bounds__(kThreads, 10) render_batch_kernel(const gs_ren
                 reinterpret_cast<const uint32_t *>(&desc->jobs[lo])[threadIdx.x];
         __syncthreads();
         const int tile = (int)(w - s_job.tile_begin);
-        render_tile<false>(sm, s_job, reinterpret_cast<const uint2 *>(s_job.ranges)[tile], tile, nullptr, nullptr);
+        render_tile<false, false>(sm, s_job, reinterpret_cast<const uint2 *>(s_job.ranges)[tile], tile, nullptr,
+                                  nullptr, nullptr);
         // render_tile ended with a barrier: nobody reads s_w any more
         if (threadIdx.x == 0) s_w = next;
         __syncthreads();
@@ -255,17 +276,23 @@ __global__ void __launch_bounds__(kThreads, 10) render_batch_kernel(const gs_ren
 }  // namespace
 
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
-                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
+                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
                           uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream) {
     const int num_tiles = cam.tiles_x * cam.tiles_y;
-    if (n_eval)
-        render_kernel<true><<<num_tiles, kThreads, 0, stream>>>(
-            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, bg[0], bg[1],
-            bg[2], out_color, final_T, n_contrib, n_eval, tile_cycles);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+#define GS_RENDER_LAUNCH(C, D)                                                                                      \
+    render_kernel<C, D><<<num_tiles, kThreads, 0, stream>>>(splats, vals, rg, cam.width, cam.height, bg[0], bg[1], \
+                                                            bg[2], out_color, final_T, n_contrib, invdepth, n_eval, \
+                                                            tile_cycles)
+    if (n_eval && invdepth)
+        GS_RENDER_LAUNCH(true, true);
+    else if (n_eval)
+        GS_RENDER_LAUNCH(true, false);
+    else if (invdepth)
+        GS_RENDER_LAUNCH(false, true);
     else
-        render_kernel<false><<<num_tiles, kThreads, 0, stream>>>(
-            splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, bg[0], bg[1],
-            bg[2], out_color, final_T, n_contrib, nullptr, nullptr);
+        GS_RENDER_LAUNCH(false, false);
+#undef GS_RENDER_LAUNCH
     return cudaGetLastError();
 }
 

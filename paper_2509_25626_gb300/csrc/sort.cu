@@ -41,6 +41,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kIpt = kSortTileItems / kThreads;  // 16 items per thread
 constexpr int kDepthIpt = kDepthItems / kThreads;  // items per thread in the depth passes
+// Predecessors read per round trip of the depth passes' look-back (wider
+// windows measured slower).
+constexpr int kDepthWin = 8;
 constexpr int kBins = 256;
 
 constexpr uint64_t kFlagAgg = 1ull << 62;        // block aggregate published
@@ -316,7 +319,7 @@ struct SweepSmemT {
 };
 using SweepSmem = SweepSmemT<kIpt>;
 
-template <bool kFinal, int IPT, typename ValFn>
+template <bool kFinal, int IPT, int WIN, typename ValFn>
 __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t (&key)[IPT], ValFn val,
                                              uint32_t start, uint32_t n, uint32_t blk, int shift,
                                              uint32_t digit_total, uint64_t *__restrict__ state, SortHeader *hdr,
@@ -352,7 +355,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t
     uint32_t tot;
     sm.dstart[t] = block_exclusive_scan(cnt, sm.scratch, &tot);
     const uint32_t dbase = block_exclusive_scan(digit_total, sm.scratch, &tot);
-    const uint64_t excl = look_back<8>(state + t, blk, kBins, cnt, hdr);
+    const uint64_t excl = look_back<WIN>(state + t, blk, kBins, cnt, hdr);
     sm.base[t] = dbase + (uint32_t)excl;
     __syncthreads();
     uint32_t vals[IPT];
@@ -411,7 +414,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t
 // One pass over (key, value) arrays in device memory, IPT x 256 elements per
 // block.  diff_hist: the digit totals are given as a difference array (the
 // tile passes).
-template <bool kFinal, int IPT>
+template <bool kFinal, int IPT, int WIN>
 __global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -442,8 +445,8 @@ __global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(co
         dt += block_exclusive_scan(dt, sm.scratch, &tot);
     }
     auto val = [&](int k) { return (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u; };
-    rank_scatter<kFinal>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv, shift_y,
-                         tiles_x);
+    rank_scatter<kFinal, IPT, WIN>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
+                                   shift_y, tiles_x);
 }
 
 // --- step 3: instance offsets in depth order -----------------------------------
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
     __syncthreads();
-    rank_scatter<kFinal>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+    rank_scatter<kFinal, kIpt, 8>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
                          ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
 }
 
@@ -642,7 +645,7 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
     const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
     for (int p = 0; p < 4; ++p)
-        onesweep_kernel<false, kDepthIpt><<<nbd, kThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+        onesweep_kernel<false, kDepthIpt, kDepthWin><<<nbd, kThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
                                                          ws.hist_depth + kBins * p, false, ws.depth_state[p],
                                                          &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
@@ -671,12 +674,12 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
         for (int p = 1; p < passes; ++p) {
             const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
             if (p == passes - 1)
-                onesweep_kernel<true, kIpt><<<nb, kThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
+                onesweep_kernel<true, kIpt, 8><<<nb, kThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
                                                                 &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
                                                                 &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
                                                                 tx);
             else
-                onesweep_kernel<false, kIpt><<<nb, kThreads, 0, st>>>(
+                onesweep_kernel<false, kIpt, 8><<<nb, kThreads, 0, st>>>(
                     buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
                     true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }

@@ -200,6 +200,18 @@ int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint3
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
                        uint32_t *tile_cycles, void *stream);
 
+/* gs_render with optional outputs, each NULL to skip (the same per-pixel
+ * blend, so out_color, final_T and n_contrib equal gs_render's bit for bit):
+ *   invdepth [H][W] float: the inverse depth blended like a colour channel,
+ *     without background -- sum over the blended splats of
+ *     alpha T / depth (the optional output of the paper's render kernels,
+ *     Appendix B listings);
+ *   n_eval, tile_cycles: as gs_render_workload (tile_cycles needs n_eval).
+ * Device buffers, 4-byte aligned.  Errors: as gs_render. */
+int gs_render_ex(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                 const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
+                 uint32_t *n_eval, uint32_t *tile_cycles, void *stream);
+
 /* gs_sort without a caller-provided workspace, for callers that cannot
  * allocate device memory: code running inside another framework's memory
  * pool, a plugin that is handed only its input and output buffers, or a

@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     preprocess,
     render,
     render_workload,
+    render_invdepth,
     sort,
     sort_static,
     sort_status,

@@ -81,6 +81,7 @@ def lib():
         L.gs_render_batch.argtypes = [P, P, ctypes.c_int32, P]
         L.gs_render_batch.restype = ctypes.c_int
         L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P, P]
+        L.gs_render_ex.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float)] + [P] * 7
         L.gs_backward_workspace_bytes.argtypes = [c_int64]
         L.gs_backward_workspace_bytes.restype = c_size_t
         L.gs_render_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P, P,
@@ -90,8 +91,8 @@ def lib():
         L.gs_strerror.argtypes = [ctypes.c_int]
         L.gs_strerror.restype = ctypes.c_char_p
         L.gs_last_cuda_error.restype = ctypes.c_char_p
-        for name in ("gs_preprocess", "gs_sort", "gs_sort_status", "gs_render", "gs_render_workload", "gs_version",
-                     "gs_built_arch"):
+        for name in ("gs_preprocess", "gs_sort", "gs_sort_status", "gs_render", "gs_render_workload", "gs_render_ex",
+                     "gs_version", "gs_built_arch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -110,6 +111,7 @@ def check(code: int, what: str) -> int:
 def exported_symbols():
     """Names of the gs_* functions the header declares."""
     return ["gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
-            "gs_render_workload", "gs_sort_static", "gs_backward_workspace_bytes", "gs_render_backward",
+            "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
+            "gs_render_backward",
             "gs_render_batch",
             "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

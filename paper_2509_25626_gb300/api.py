@@ -212,6 +212,24 @@ def render_workload(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tens
     return out_color, final_T, n_contrib, n_eval
 
 
+def render_invdepth(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
+                    stream=None):
+    """gs_render_ex with the inverse-depth output: (image, final_T,
+    n_contrib, invdepth [H, W] float32)."""
+    dev = splats.device
+    H, W = int(cam.height), int(cam.width)
+    out_color = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    final_T = torch.empty((H, W), dtype=torch.float32, device=dev)
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    invdepth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    code = L.lib().gs_render_ex(_ptr(splats), _ptr(vals), _ptr(ranges), ctypes.byref(c), bgc, _ptr(out_color),
+                                _ptr(final_T), _ptr(n_contrib), _ptr(invdepth), None, None, _stream(stream))
+    L.check(code, "gs_render_ex")
+    return out_color, final_T, n_contrib, invdepth
+
+
 class Renderer:
     """Device buffers for rendering one scene size at one resolution.
 

@@ -23,7 +23,7 @@ cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, cons
                                    float *dsplat, const gs_scene_grads &g, cudaStream_t st);
 cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
-                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
+                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
                           uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream);
 
 static thread_local char g_cuda_err[256] = "no CUDA error recorded";
@@ -124,7 +124,7 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream) {
 
 static int render_common(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                          const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib,
-                         uint32_t *n_eval, uint32_t *tile_cycles, void *stream) {
+                         float *invdepth, uint32_t *n_eval, uint32_t *tile_cycles, void *stream) {
     if (!camera_ok(cam) || !bg || !ranges || !aligned(ranges, 8)) return GS_ERR_INVALID_ARG;
     if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
     if (!out_color || !final_T || !n_contrib || !aligned(out_color, 4) || !aligned(final_T, 4) ||
@@ -134,19 +134,31 @@ static int render_common(const gs_splat *splats, const uint32_t *vals, const uin
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
     return cuda_status(launch_render(splats, vals, ranges, make_cam_params(*cam), bg, out_color, final_T, n_contrib,
-                                     n_eval, tile_cycles, (cudaStream_t)stream));
+                                     invdepth, n_eval, tile_cycles, (cudaStream_t)stream));
 }
 
 int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
               const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream) {
-    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, nullptr, stream);
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, nullptr, nullptr,
+                         stream);
 }
 
 int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
                        uint32_t *tile_cycles, void *stream) {
     if (!n_eval || !aligned(n_eval, 4) || (tile_cycles && !aligned(tile_cycles, 4))) return GS_ERR_INVALID_ARG;
-    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, n_eval, tile_cycles, stream);
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, n_eval, tile_cycles,
+                         stream);
+}
+
+int gs_render_ex(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                 const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
+                 uint32_t *n_eval, uint32_t *tile_cycles, void *stream) {
+    if ((invdepth && !aligned(invdepth, 4)) || (n_eval && !aligned(n_eval, 4)) ||
+        (tile_cycles && (!n_eval || !aligned(tile_cycles, 4))))
+        return GS_ERR_INVALID_ARG;
+    return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, invdepth, n_eval, tile_cycles,
+                         stream);
 }
 
 int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t grid, void *stream) {

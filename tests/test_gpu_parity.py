@@ -170,6 +170,33 @@ def test_workload_counts_match_oracle(case, oracle_frames):
         assert cyc[lens > np.median(lens[lens > 0])].mean() > cyc[lens == 0].mean()
 
 
+@pytest.mark.parametrize("case", [c[0] for c in SMALL])
+def test_invdepth_parity(case, oracle_frames):
+    """The optional inverse-depth output (gs_render_ex) on the oracle's
+    records: within 2e-4 (relative above 1) of the oracle's FP64 sum of
+    alpha T / z on every pixel with no near decision, and the image, final T
+    and n_contrib equal gs_render's bit for bit."""
+    name, sc, cam = next(c for c in SMALL if c[0] == case)
+    pre, srt, img = oracle_frames[name]
+    rec = to_dev_records(records_from_oracle(pre, SPLAT_DTYPE))
+    vals = torch.from_numpy(np.ascontiguousarray(srt["vals"]).view(np.int32).copy() if srt["m"] else
+                            np.zeros(1, np.int32)).to(DEV)
+    ranges = torch.from_numpy(srt["ranges"].view(np.int32).copy()).to(DEV)
+    bg = (0.1, 0.2, 0.3)
+    out_d, T_d, nc_d, inv = gs.render_invdepth(rec, vals, ranges, cam, bg)
+    out, T, nc = gs.render(rec, vals, ranges, cam, bg=bg)
+    torch.cuda.synchronize()
+    assert torch.equal(out_d, out) and torch.equal(T_d, T) and torch.equal(nc_d, nc)
+    inv = inv.cpu().numpy().astype(np.float64)
+    ref = img["invdepth"]
+    exact = img["near"] == 0
+    err = np.abs(inv - ref)
+    bad = (err > 2e-4 * np.maximum(1.0, np.abs(ref))) & exact
+    assert not np.any(bad), f"{bad.sum()} pixels off, max {err[bad].max():.3e}"
+    assert ref.max() > 0.1
+    print(name, "invdepth max err", float(err[exact].max()), "range", float(ref.min()), float(ref.max()))
+
+
 def test_batches_stop_permanently(oracle):
     """A tile with 600 stacked splats that saturates in the first batch of
     256: the pixel must not resume in later batches (a failure mode the

@@ -237,35 +237,52 @@ __global__ void __launch_bounds__(kThreads, 10) render_kernel(const gs_splat *__
 // (job, tile) each, numbered through the jobs' tile_begin prefix -- from an
 // atomic counter until all are taken.  Each block asks for its next item
 // when it starts the current one, so the atomic's round trip overlaps the
-// blend.  The job table and its counts live in device memory, so one
-// captured launch serves any batch.  Held to the register count of
-// render_kernel so as many blocks stay resident per SM.
+// blend, and keeps the job table (up to 64 jobs) in shared memory, so
+// finding an item's job costs no global round trip.  The job table and its
+// counts live in device memory, so one captured launch serves any batch.
+// Held to the register count of render_kernel so as many blocks stay
+// resident per SM.
 __global__ void __launch_bounds__(kThreads, 10) render_batch_kernel(const gs_render_batch_desc *__restrict__ desc,
                                                                 uint32_t *__restrict__ counter) {
+    constexpr int kJobsCached = 64;  // job tables up to this size live in shared memory
+    constexpr int kJobWords = (int)(sizeof(gs_render_job) / 4);
+    static_assert(sizeof(gs_render_job) % 4 == 0 && kJobWords <= kThreads, "job copy");
     __shared__ RenderSmem sm;
-    __shared__ gs_render_job s_job;
+    __shared__ gs_render_job s_jobs[kJobsCached];
     __shared__ uint32_t s_w;
-    static_assert(sizeof(gs_render_job) % 4 == 0 && sizeof(gs_render_job) / 4 <= kThreads, "job copy");
     const int n_jobs = desc->n_jobs;
     const uint32_t total = desc->total_tiles;
+    const bool cached = n_jobs <= kJobsCached;  // uniform
+    if (cached)
+        for (int i = threadIdx.x; i < n_jobs * kJobWords; i += kThreads)
+            reinterpret_cast<uint32_t *>(s_jobs)[i] = reinterpret_cast<const uint32_t *>(desc->jobs)[i];
     if (threadIdx.x == 0) s_w = atomicAdd(counter, 1u);
     __syncthreads();
     for (uint32_t w = s_w; w < total;) {
         uint32_t next = 0;
         if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
         int lo = 0, hi = n_jobs;  // last job with tile_begin <= w
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (desc->jobs[mid].tile_begin <= w) lo = mid; else hi = mid;
+        if (cached) {
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_jobs[mid].tile_begin <= w) lo = mid; else hi = mid;
+            }
+        } else {
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (desc->jobs[mid].tile_begin <= w) lo = mid; else hi = mid;
+            }
+            // the previous tile ended with a barrier, so slot 0 is free
+            if (threadIdx.x < kJobWords)
+                reinterpret_cast<uint32_t *>(&s_jobs[0])[threadIdx.x] =
+                    reinterpret_cast<const uint32_t *>(&desc->jobs[lo])[threadIdx.x];
+            __syncthreads();
+            lo = 0;
         }
-        // the previous tile ended with a barrier, so s_job is free
-        if (threadIdx.x < sizeof(gs_render_job) / 4)
-            reinterpret_cast<uint32_t *>(&s_job)[threadIdx.x] =
-                reinterpret_cast<const uint32_t *>(&desc->jobs[lo])[threadIdx.x];
-        __syncthreads();
-        const int tile = (int)(w - s_job.tile_begin);
-        render_tile<false, false>(sm, s_job, reinterpret_cast<const uint2 *>(s_job.ranges)[tile], tile, nullptr,
-                                  nullptr, nullptr);
+        const gs_render_job &job = s_jobs[lo];
+        const int tile = (int)(w - job.tile_begin);
+        render_tile<false, false>(sm, job, reinterpret_cast<const uint2 *>(job.ranges)[tile], tile, nullptr, nullptr,
+                                  nullptr);
         // render_tile ended with a barrier: nobody reads s_w any more
         if (threadIdx.x == 0) s_w = next;
         __syncthreads();

@@ -305,34 +305,33 @@ def main():
     fps = whole_job_rate(args.steps, world, t_ms)
 
     # end to end through the public API: scene from pinned host memory each
-    # step, image back to pinned host memory
+    # step, image back to pinned host memory; FramePipeline overlaps the
+    # upload of frame k+1 with the render of frame k
     e2e = None
     if not args.no_e2e:
         host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in scene.arrays()]
-        himg = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
         h2d = sum(h.numel() * h.element_size() for h in host)
-        d2h = himg.numel() * himg.element_size()
-        dst = [st.means, st.log_scales, st.quats, st.opacity_logits, st.sh]
-        for k in range(2):
-            for d_, h_ in zip(dst, host):
-                d_.copy_(h_, non_blocking=True)
-            r.frame(st, cams[pose_of(k)])
-            himg.copy_(r.image, non_blocking=True)
+        d2h = 3 * H * W * 4
+        pipe = gs.FramePipeline(n, W, H, m_cap, dev)
+        for k in range(3):
+            pipe.result(pipe.submit(host, cams[pose_of(k)]))
         torch.cuda.synchronize(dev)
         barrier()
         s2, e2 = E(), E()
-        s2.record(stream)
+        s2.record(pipe.h2d)
         for k in range(args.steps):
-            for d_, h_ in zip(dst, host):
-                d_.copy_(h_, non_blocking=True)
-            r.frame(st, cams[pose_of(k)])
-            himg.copy_(r.image, non_blocking=True)
-        e2.record(stream)
+            pipe.submit(host, cams[pose_of(k)])
+        e2.record(pipe.d2h)
         torch.cuda.synchronize(dev)
         barrier()
+        for t in (pipe.k - 2, pipe.k - 1):
+            m_e, over_e = pipe.instances(t)
+            assert not over_e, "instance capacity overflow in the end-to-end frames"
         te = max_over_ranks(s2.elapsed_time(e2), world, dev)
         e2e = dict(value=whole_job_rate(args.steps, world, te), unit="frames/s", h2d_bytes_per_step=h2d,
-                   d2h_bytes_per_step=d2h)
+                   d2h_bytes_per_step=d2h, h2d_gbs=h2d * args.steps / (te / 1e3) / 1e9,
+                   note="FramePipeline: uploads of frame k+1 overlap the render of frame k")
+        del pipe
 
     # the render with the optional inverse-depth output (outside the timed frames)
     inv = torch.empty((H, W), dtype=torch.float32, device=dev)

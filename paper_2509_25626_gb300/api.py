@@ -263,6 +263,79 @@ class Renderer:
         return sort_status(self.workspace, stream)
 
 
+class FramePipeline:
+    """End-to-end frames from host memory, double-buffered.
+
+    Each ``submit`` uploads a scene from pinned host memory, renders it and
+    reads the image back to pinned host memory -- every step of a frame,
+    every frame -- but on three streams: the upload of frame k+1 runs while
+    frame k renders, and the read-back of frame k runs while frame k+1 is
+    uploaded.  Two slots (device scene, Renderer, host image) alternate; a
+    slot is reused only after its previous frame's image has been read back.
+    The host-to-device link, not the GPU, bounds the rate for large scenes.
+    """
+
+    class _Slot:
+        def __init__(self, n, width, height, m_cap, device):
+            f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=device)
+            self.scene = SceneTensors(f(n, 3), f(n, 3), f(n, 4), f(n), f(n, 16, 3))
+            self.renderer = Renderer(n, width, height, m_cap, device)
+            self.host_image = torch.empty((3, height, width), dtype=torch.float32).pin_memory()
+            self.h2d_done = torch.cuda.Event()
+            self.d2h_done = torch.cuda.Event()
+            self.ticket = -1
+
+    def __init__(self, n: int, width: int, height: int, m_cap: int, device="cuda"):
+        self.device = torch.device(device)
+        self.slots = [self._Slot(int(n), int(width), int(height), int(m_cap), self.device) for _ in range(2)]
+        self.h2d = torch.cuda.Stream(self.device)
+        self.compute = torch.cuda.Stream(self.device)
+        self.d2h = torch.cuda.Stream(self.device)
+        self.k = 0
+
+    def submit(self, host_arrays, cam, bg=(0.0, 0.0, 0.0), sh_degree: int = 3) -> int:
+        """Enqueue one frame.  host_arrays: pinned CPU tensors (means,
+        log_scales, quats, opacity_logits, sh), kept unchanged until the
+        frame's upload has run.  Returns a ticket for ``result``."""
+        slot = self.slots[self.k % 2]
+        dst = [slot.scene.means, slot.scene.log_scales, slot.scene.quats, slot.scene.opacity_logits, slot.scene.sh]
+        slot.scene.sh_degree = int(sh_degree)
+        self.h2d.wait_event(slot.d2h_done)  # the slot's previous frame is finished and read back
+        with torch.cuda.stream(self.h2d):
+            for d, h in zip(dst, host_arrays):
+                if not h.is_pinned() or h.shape != d.shape or h.dtype != torch.float32:
+                    raise ValueError("host arrays must be pinned float32 tensors of the pipeline's scene size")
+                d.copy_(h, non_blocking=True)
+            slot.h2d_done.record(self.h2d)
+        self.compute.wait_event(slot.h2d_done)
+        with torch.cuda.stream(self.compute):
+            image, _, _ = slot.renderer.frame(slot.scene, cam, bg)
+            done = torch.cuda.Event()
+            done.record(self.compute)
+        self.d2h.wait_event(done)
+        with torch.cuda.stream(self.d2h):
+            slot.host_image.copy_(image, non_blocking=True)
+            slot.d2h_done.record(self.d2h)
+        slot.ticket = self.k
+        self.k += 1
+        return slot.ticket
+
+    def result(self, ticket: int) -> torch.Tensor:
+        """The host image of frame ``ticket`` (waits for it).  Valid until
+        the frame two submits later reuses the slot."""
+        slot = self.slots[ticket % 2]
+        if slot.ticket != ticket:
+            raise ValueError("frame already overwritten (only the last two frames are kept)")
+        slot.d2h_done.synchronize()
+        return slot.host_image
+
+    def instances(self, ticket: int):
+        """(M, overflow) of frame ``ticket`` (synchronises)."""
+        slot = self.slots[ticket % 2]
+        slot.d2h_done.synchronize()
+        return slot.renderer.instances()
+
+
 def render_backward(scene: SceneTensors, cam, splats, vals, ranges, final_T, n_contrib, dL_dcolor,
                     bg=(0.0, 0.0, 0.0), workspace=None, stream=None):
     """gs_render_backward: gradients of sum(dL_dcolor * image) with respect to

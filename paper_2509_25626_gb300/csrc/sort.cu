@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(co
 // Also, if the instances overflow the caller's capacity, takes the dropped
 // ones (global index >= m_cap) out of the tile digit counts, so that the
 // counts match the instances the tile passes sort.
-__global__ void __launch_bounds__(kThreads) offsets_kernel(SortWs ws, uint64_t m_cap, TileKeyLayout tl) {
+__global__ void __launch_bounds__(kThreads, 3) offsets_kernel(SortWs ws, uint64_t m_cap, TileKeyLayout tl) {
     __shared__ uint64_t scratch[33];
     __shared__ uint32_t s_slot;
     const uint32_t n = ws.hdr->nvis;

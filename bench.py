@@ -43,6 +43,7 @@ def parse_args():
     p.add_argument("--no-backward", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-multiview", action="store_true")
+    p.add_argument("--inflight", type=int, default=3, help="frames in flight on separate streams")
     p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
     return p.parse_args()
 
@@ -268,20 +269,54 @@ def main():
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: rank_pose(k, world, rank, P)
-
-    for k in range(args.warmup):
-        r.frame(st, cams[pose_of(k)])
-    torch.cuda.synchronize(dev)
-
     E = lambda: torch.cuda.Event(enable_timing=True)
-    ev = [[E() for _ in range(4)] for _ in range(args.steps)]
+
+    # frames in flight: frame k runs on stream k % F with its own buffers, so
+    # one frame's latency-bound sort and the tail of its render overlap the
+    # next frame's work; every frame still runs the whole path
+    F = max(1, args.inflight)
+    rs = [r] + [gs.Renderer(n, W, H, m_cap, dev) for _ in range(F - 1)]
+    streams = [torch.cuda.Stream(dev) for _ in range(F)]
+
+    def run_frames(k0, count, timed):
+        fork = E() if timed else torch.cuda.Event()
+        fork.record(stream)
+        for s_ in streams:
+            s_.wait_event(fork)
+        for k in range(count):
+            i = k % F
+            with torch.cuda.stream(streams[i]):
+                rs[i].frame(st, cams[pose_of(k0 + k)])
+        for s_ in streams:
+            j = torch.cuda.Event()
+            j.record(s_)
+            stream.wait_event(j)
+
+    run_frames(0, args.warmup, False)
+    torch.cuda.synchronize(dev)
     start, end = E(), E()
     sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
     start.record(stream)
-    for k in range(args.steps):
+    run_frames(args.warmup, args.steps, True)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier()
+    t_ms = start.elapsed_time(end)
+    for r_ in rs:
+        assert not r_.instances()[1], "instance capacity overflow during the timed region"
+    t_ms = max_over_ranks(t_ms, world, dev)
+    fps = whole_job_rate(args.steps, world, t_ms)
+
+    # per-stage times, one frame at a time on one stream (not the headline)
+    ks = min(args.steps, 200)
+    ev = [[E() for _ in range(4)] for _ in range(ks)]
+    s1, e1 = E(), E()
+    s1.record(stream)
+    for k in range(ks):
         cam = cams[pose_of(args.warmup + k)]
         e = ev[k]
         e[0].record(stream)
@@ -291,18 +326,13 @@ def main():
         e[2].record(stream)
         gs.render(r.splats, r.vals, r.ranges, cam, (0.0, 0.0, 0.0), r.image, r.final_T, r.n_contrib)
         e[3].record(stream)
-    end.record(stream)
+    e1.record(stream)
     torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    barrier()
-    t_ms = start.elapsed_time(end)
-    pre_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
-    sort_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
-    rend_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
-    m_last, over = r.instances()
-    assert not over, "instance capacity overflow during the timed region"
-    t_ms = max_over_ranks(t_ms, world, dev)
-    fps = whole_job_rate(args.steps, world, t_ms)
+    serial_fps = ks / (s1.elapsed_time(e1) / 1000.0)
+    pre_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / ks
+    sort_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / ks
+    rend_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / ks
+    assert not r.instances()[1], "instance capacity overflow in the per-stage frames"
 
     # end to end through the public API: scene from pinned host memory each
     # step, image back to pinned host memory; FramePipeline overlaps the
@@ -358,7 +388,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s at the max SM clock
-    used = [pose_of(args.warmup + k) for k in range(args.steps)]
+    used = [pose_of(args.warmup + k) for k in range(ks)]
     evals_mean = statistics.mean(evals[p] for p in used)
     ms_mean = statistics.mean(ms[p] for p in used)
     render_tflops = evals_mean * FLOP_PER_EVAL / (rend_ms / 1000.0) / 1e12
@@ -417,7 +447,8 @@ def main():
             dtype="f32", data="synthetic",
             config=dict(workload=args.workload, gaussians=n, width=W, height=H, poses=P, tiles=T,
                         instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
-                        m_cap=m_cap, parallelism=f"replicas{world}",
+                        m_cap=m_cap, parallelism=f"replicas{world}", frames_in_flight=F,
+                        serial_frames_per_s=serial_fps,
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
             roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, serving=serving, multiview=multiview,
             backward=backward,

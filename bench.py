@@ -265,7 +265,7 @@ def main():
     vis = []
     for cam in cams[:1]:
         gs.preprocess(st, cam, r.splats)
-        vis.append(int((r.splats.view(torch.int32)[:, 13] > 0).sum().item()))  # tiles_touched
+        vis.append(int((r.splats.view(torch.int32)[:n, 13] > 0).sum().item()))  # tiles_touched
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: rank_pose(k, world, rank, P)
@@ -392,7 +392,7 @@ def main():
     evals_mean = statistics.mean(evals[p] for p in used)
     ms_mean = statistics.mean(ms[p] for p in used)
     render_tflops = evals_mean * FLOP_PER_EVAL / (rend_ms / 1000.0) / 1e12
-    pre_bytes = n * (236 + 64)
+    pre_bytes = n * (236 + 64 + 16)  # scene in; record and dense sort inputs out
     pre_gbs = pre_bytes / (pre_ms / 1000.0) / 1e9
     traffic = None
     try:

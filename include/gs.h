@@ -94,7 +94,22 @@ typedef struct gs_splat {
     uint32_t tiles_touched;   /* (x1 - x0) (y1 - y0) */
     uint32_t rect_lo;         /* x0 | y0 << 16, tile rectangle, inclusive */
     uint32_t rect_hi;         /* x1 | y1 << 16, exclusive */
-} gs_splat;  /* the last four words (the sort's inputs) share one 16-byte vector */
+} gs_splat;
+
+/* The sort's inputs of one splat, 16 bytes: the last four words of its
+ * record, repeated.  gs_preprocess writes them a second time, densely, after
+ * the n records of the splat buffer, so that gs_sort reads 16 bytes per
+ * Gaussian instead of a 64-byte record (DRAM moves whole 64-byte
+ * granules). */
+typedef struct gs_sort_input {
+    uint32_t depth_bits;    /* float bits of gs_splat.depth */
+    uint32_t tiles_touched;
+    uint32_t rect_lo, rect_hi;
+} gs_sort_input;
+
+/* Bytes of a splat buffer for n Gaussians: n gs_splat records followed by n
+ * gs_sort_input vectors (80 n bytes). */
+size_t gs_splat_buffer_bytes(int64_t n);
 
 /* Section II-B (1), projection step.  One thread per Gaussian:
  *   z = V.[m, 1] (FP32, fmaf(V22, mz, fmaf(V21, my, fmaf(V20, mx, V23))));
@@ -104,8 +119,9 @@ typedef struct gs_splat {
  *   radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
  *   rect = [floor((p - r) / 16), floor((p + r + 15) / 16)) clamped to the grid; cull if empty;
  *   colour = max(sum_lm c_lm Y_lm(dir) + 0.5, 0), dir from the camera centre to the mean.
- * scene: device arrays; cam: host struct; splats: device, [scene->n] records,
- * 16-byte aligned.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+ * scene: device arrays; cam: host struct; splats: device splat buffer of
+ * gs_splat_buffer_bytes(n) bytes, 16-byte aligned: [n] records, then [n]
+ * gs_sort_input.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, void *stream);
 
 /* Bytes of device workspace gs_sort needs for n Gaussians, m_cap tile
@@ -120,7 +136,8 @@ size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles);
  * ascending id); ranges[t] = [start, end) of tile t's instances in the sorted
  * list, [0, 0) for an empty tile (Algorithm 1, "load work range").
  *
- * splats: device, [n] records from gs_preprocess with the same camera.
+ * splats: device splat buffer from gs_preprocess with the same camera
+ * (gs_sort reads its gs_sort_input part, after the n records).
  * keys, vals: device, capacity m_cap each (8- and 4-byte elements, 16-byte
  * aligned); on return the first M entries hold the sorted instances.
  * ranges: device, [num_tiles][2] uint32.

@@ -21,4 +21,5 @@ from .api import (  # noqa: F401
     sort_static,
     sort_status,
     sort_workspace_bytes,
+    splat_buffer,
 )

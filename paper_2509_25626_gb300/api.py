@@ -86,11 +86,19 @@ class SceneTensors:
         return s
 
 
+def splat_buffer(n: int, device="cuda") -> torch.Tensor:
+    """A splat buffer for n Gaussians (gs_splat_buffer_bytes): float32 rows of
+    16, the first n rows the records, then the dense sort inputs (4 per row)."""
+    n = max(int(n), 1)
+    return torch.empty((n + (n + 3) // 4, 16), dtype=torch.float32, device=device)
+
+
 def preprocess(scene: SceneTensors, cam, splats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """gs_preprocess: returns float32 [n, 16] splat records."""
+    """gs_preprocess: returns the splat buffer (float32 rows of 16; rows
+    [0, n) are the records)."""
     n = scene.n
     if splats is None:
-        splats = torch.empty((max(n, 1), 16), dtype=torch.float32, device=scene.means.device)
+        splats = splat_buffer(n, scene.means.device)
     _check_tensor(splats, torch.float32, "splats")
     c = camera_struct(cam)
     L.check(L.lib().gs_preprocess(ctypes.byref(scene.struct()), ctypes.byref(c), _ptr(splats), _stream(stream)),
@@ -241,7 +249,7 @@ class Renderer:
         self.n, self.width, self.height, self.m_cap = int(n), int(width), int(height), int(m_cap)
         T = ((self.width + 15) // 16) * ((self.height + 15) // 16)
         dev = torch.device(device)
-        self.splats = torch.empty((max(self.n, 1), 16), dtype=torch.float32, device=dev)
+        self.splats = splat_buffer(self.n, dev)
         self.keys = torch.empty(max(self.m_cap, 1), dtype=torch.int64, device=dev)
         self.vals = torch.empty(max(self.m_cap, 1), dtype=torch.int32, device=dev)
         self.ranges = torch.empty((T, 2), dtype=torch.int32, device=dev)

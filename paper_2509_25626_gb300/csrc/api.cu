@@ -26,6 +26,8 @@ cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const ui
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
                           uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream);
 
+static_assert(sizeof(gs_splat) == 64 && sizeof(gs_sort_input) == 16, "splat buffer layout");
+
 static thread_local char g_cuda_err[256] = "no CUDA error recorded";
 
 void set_cuda_error(cudaError_t e) {
@@ -165,6 +167,8 @@ int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t
     if (!desc || !aligned(desc, 8) || !counter || !aligned(counter, 4) || grid < 0) return GS_ERR_INVALID_ARG;
     return cuda_status(launch_render_batch(desc, counter, grid, (cudaStream_t)stream));
 }
+
+size_t gs_splat_buffer_bytes(int64_t n) { return (size_t)(n > 0 ? n : 0) * (sizeof(gs_splat) + sizeof(gs_sort_input)); }
 
 size_t gs_backward_workspace_bytes(int64_t n) { return (size_t)(n > 0 ? n : 1) * 12 * sizeof(float); }
 

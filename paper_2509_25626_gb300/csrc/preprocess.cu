@@ -37,12 +37,13 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
     return dop + err;
 }
 
-__device__ __forceinline__ void write_culled(gs_splat *out, float depth) {
+__device__ __forceinline__ void write_culled(gs_splat *out, uint4 *sort_in, float depth) {
     float4 *o = reinterpret_cast<float4 *>(out);
     o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     o[2] = make_float4(0.f, -1.f, -1.f, 0.f);     // b, cull box empty, radius = 0
     o[3] = make_float4(depth, 0.f, 0.f, 0.f);     // depth, tiles = 0, rect 0
+    *sort_in = make_uint4(__float_as_uint(depth), 0u, 0u, 0u);
 }
 
 __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict__ means,
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
                                                          const float4 *__restrict__ quats,
                                                          const float *__restrict__ logits,
                                                          const float4 *__restrict__ sh, int64_t n, int sh_degree,
-                                                         CamParams cam, gs_splat *__restrict__ out) {
+                                                         CamParams cam, gs_splat *__restrict__ out,
+                                                         uint4 *__restrict__ sort_in) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     // Depth in the exact form the sort key is defined with.
     const float z = fmaf(V[10], mz, fmaf(V[9], my, fmaf(V[8], mx, V[11])));
     if (!(z > kNearZ)) {
-        write_culled(out + g, z);
+        write_culled(out + g, sort_in + g, z);
         return;
     }
     const float tx = fmaf(V[2], mz, fmaf(V[1], my, fmaf(V[0], mx, V[3])));
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     const uint32_t x0 = (uint32_t)fx0, y0 = (uint32_t)fy0, x1 = (uint32_t)fx1, y1 = (uint32_t)fy1;
     const uint32_t tiles = (x1 - x0) * (y1 - y0);
     if (tiles == 0u) {
-        write_culled(out + g, z);
+        write_culled(out + g, sort_in + g, z);
         return;
     }
 
@@ -202,7 +204,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     o[0] = make_float4(x, y, w00, w01);
     o[1] = make_float4(w11, log2_opacity, rgb[0], rgb[1]);
     o[2] = make_float4(rgb[2], hx, hy, __int_as_float((int)radius));
-    o[3] = make_float4(z, __uint_as_float(tiles), __uint_as_float(x0 | (y0 << 16)), __uint_as_float(x1 | (y1 << 16)));
+    const uint4 si = make_uint4(__float_as_uint(z), tiles, x0 | (y0 << 16), x1 | (y1 << 16));
+    o[3] = make_float4(__uint_as_float(si.x), __uint_as_float(si.y), __uint_as_float(si.z), __uint_as_float(si.w));
+    sort_in[g] = si;  // the dense copy gs_sort reads
 }
 
 }  // namespace
@@ -213,7 +217,7 @@ cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat 
     const int64_t blocks = (s.n + threads - 1) / threads;
     preprocess_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
         s.means, s.log_scales, reinterpret_cast<const float4 *>(s.quats), s.opacity_logits,
-        reinterpret_cast<const float4 *>(s.sh), s.n, s.sh_degree, cam, out);
+        reinterpret_cast<const float4 *>(s.sh), s.n, s.sh_degree, cam, out, reinterpret_cast<uint4 *>(out + s.n));
     return cudaGetLastError();
 }
 

@@ -241,12 +241,13 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
     for (int i = threadIdx.x; i < kMaxTilePasses * (kBins + 1); i += kThreads) (&s_tdiff[0][0])[i] = 0;
     const uint32_t blk = dynamic_block(&ws.hdr->tile_ctr[kCtrCompact], &s_slot);
     const int64_t base = (int64_t)blk * kSortTileItems + (int64_t)threadIdx.x * kIpt;  // 16 consecutive per thread
-    // (depth, tiles, rect lo, rect hi): one 16-byte vector per record
+    // (depth, tiles, rect lo, rect hi): the dense copy after the n records
+    const uint4 *__restrict__ sort_in = reinterpret_cast<const uint4 *>(splats + n);
     uint4 r4[kIpt];
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const int64_t i = base + k;
-        r4[k] = i < n ? __ldg(reinterpret_cast<const uint4 *>(splats + i) + 3) : make_uint4(0u, 0u, 0u, 0u);
+        r4[k] = i < n ? __ldg(sort_in + i) : make_uint4(0u, 0u, 0u, 0u);
     }
     uint32_t vis = 0;  // bit k: element base + k is visible
 #pragma unroll

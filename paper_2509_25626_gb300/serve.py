@@ -25,7 +25,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .api import SceneTensors, camera_struct, num_tiles, preprocess, render, sort, sort_workspace_bytes
+from .api import SceneTensors, camera_struct, num_tiles, preprocess, render, sort, sort_workspace_bytes, splat_buffer
 
 JOB_BYTES = 72
 DESC_HEADER = 16
@@ -57,7 +57,7 @@ class _Slot:
     def __init__(self, n, cam, m_cap, device):
         T = num_tiles(cam)
         H, W = int(cam.height), int(cam.width)
-        self.splats = torch.empty((max(n, 1), 16), dtype=torch.float32, device=device)
+        self.splats = splat_buffer(n, device)
         self.keys = torch.empty(max(m_cap, 1), dtype=torch.int64, device=device)
         self.vals = torch.empty(max(m_cap, 1), dtype=torch.int32, device=device)
         self.ranges = torch.empty((T, 2), dtype=torch.int32, device=device)

@@ -27,10 +27,15 @@ def gpu_records(scene, cam):
 
 
 def to_dev_records(rec: np.ndarray) -> torch.Tensor:
+    """A splat buffer holding these records: the records, then their dense
+    sort inputs (the last 16 bytes of each record again)."""
     arr = np.ascontiguousarray(rec).view(np.float32).reshape(-1, 16)
     if arr.shape[0] == 0:
         arr = np.zeros((1, 16), np.float32)
-    return torch.from_numpy(arr.copy()).to(DEV)
+    n = arr.shape[0]
+    tail = np.zeros(((n + 3) // 4) * 4 * 4, np.float32)
+    tail[: 4 * n] = arr[:, 12:16].reshape(-1)
+    return torch.from_numpy(np.concatenate([arr.reshape(-1), tail]).reshape(-1, 16)).to(DEV)
 
 
 def gpu_sort(splats_t, n, cam, m_cap=None):
@@ -76,6 +81,21 @@ def test_preprocess_parity(case, oracle_frames):
     rep = compare_preprocess(gpu_records(sc, cam), pre, cam)
     print(name, rep)
     assert rep["visible"] > 0
+
+
+def test_splat_buffer_sort_inputs_repeat_the_records():
+    """gs_preprocess writes each record's last 16 bytes a second time,
+    densely, after the n records; the buffer has gs_splat_buffer_bytes."""
+    from paper_2509_25626_gb300 import _lib as L
+    name, sc, cam = SMALL[3]
+    sp = gs.preprocess(SceneTensors.from_scene(sc, DEV), cam)
+    torch.cuda.synchronize()
+    n = sc.n
+    assert sp.numel() * 4 >= L.lib().gs_splat_buffer_bytes(n) == 80 * n
+    words = sp.view(torch.int32).cpu().numpy().reshape(-1)
+    recs = words[: 16 * n].reshape(n, 16)
+    tail = words[16 * n: 16 * n + 4 * n].reshape(n, 4)
+    assert np.array_equal(tail, recs[:, 12:16])
 
 
 @pytest.mark.parametrize("case", [c[0] for c in SMALL])

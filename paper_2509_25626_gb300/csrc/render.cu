@@ -206,7 +206,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
 }
 
 template <bool kCount, bool kDepth>
-__global__ void __launch_bounds__(kThreads, 10) render_kernel(const gs_splat *__restrict__ splats,
+__global__ void __launch_bounds__(kThreads, (kCount || kDepth) ? 10 : 12) render_kernel(const gs_splat *__restrict__ splats,
                                                           const uint32_t *__restrict__ vals,
                                                           const uint2 *__restrict__ ranges, int width, int height,
                                                           float bg_r, float bg_g, float bg_b,

@@ -230,19 +230,48 @@ constexpr float kSH3c = 0.4570457994644658f;
 constexpr float kSH3d = 0.3731763325901154f;
 constexpr float kSH3e = 1.445305721320277f;
 
-__global__ void __launch_bounds__(128) preprocess_backward_kernel(
+constexpr int kPreBackThreads = 128;
+constexpr int kShStride = 49;  // 48 floats + 1: rows start in different banks
+
+__device__ __forceinline__ void preprocess_backward_one(
+    const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
+    const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
+    const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
+    float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits);
+
+__global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
     const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
     const float *__restrict__ logits, const float *__restrict__ sh, int64_t n, int sh_degree, CamParams cam,
     const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
     float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits,
     float *__restrict__ dsh) {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= n) return;
+    // The block's SH coefficients pass through shared memory both ways, so
+    // global loads and stores are coalesced (one thread's 48 floats span 192
+    // bytes); a thread reads its own row and overwrites it with its gradient.
+    __shared__ float s_sh[kPreBackThreads][kShStride];
+    const int64_t g0 = (int64_t)blockIdx.x * kPreBackThreads;
+    const int nb = (int)min((int64_t)kPreBackThreads, n - g0);  // Gaussians of this block
+    for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) s_sh[f / 48][f % 48] = sh[g0 * 48 + f];
+    __syncthreads();
+    const int64_t gi = g0 + threadIdx.x;
+    if (gi < n) preprocess_backward_one(means, log_scales, quats, logits, s_sh[threadIdx.x], gi, sh_degree, cam,
+                                        splats, dsplat, dmeans, dlog_scales, dquats, dlogits);
+    __syncthreads();
+    for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) dsh[g0 * 48 + f] = s_sh[f / 48][f % 48];
+}
+
+// One Gaussian of preprocess_backward_kernel; shg: its 48 SH coefficients,
+// replaced by their gradients on return.
+__device__ __forceinline__ void preprocess_backward_one(
+    const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
+    const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
+    const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
+    float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits) {
     const uint32_t tiles = reinterpret_cast<const uint32_t *>(splats + gi)[rec::kTiles];
     float *dm = dmeans + 3 * gi;
     float *dls = dlog_scales + 3 * gi;
     float *dq = dquats + 4 * gi;
-    float *dshg = dsh + 48 * gi;
+    float *dshg = shg;
     if (tiles == 0u) {  // culled: appears in no list
         for (int k = 0; k < 3; ++k) dm[k] = dls[k] = 0.f;
         for (int k = 0; k < 4; ++k) dq[k] = 0.f;
@@ -399,7 +428,6 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
     Gz[14] = kSH3e * (xx - yy);
     Y[15] = -kSH3a * x * (xx - 3.f * yy); Gx[15] = -3.f * kSH3a * (xx - yy); Gy[15] = 6.f * kSH3a * x * y; Gz[15] = 0.f;
     const int ncoef = (sh_degree + 1) * (sh_degree + 1);
-    const float *shg = sh + 48 * gi;
     // clamped channels (raw < 0) pass no gradient
     for (int ch = 0; ch < 3; ++ch) {
         float raw = 0.5f;
@@ -411,8 +439,8 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(
         const bool on = k < ncoef;
         float gY = 0.f;
         for (int ch = 0; ch < 3; ++ch) {
+            gY = fmaf(grgb[ch], on ? shg[3 * k + ch] : 0.f, gY);  // read before the gradient overwrites it
             dshg[3 * k + ch] = on ? grgb[ch] * Y[k] : 0.f;
-            gY = fmaf(grgb[ch], on ? shg[3 * k + ch] : 0.f, gY);
         }
         gdx = fmaf(gY, Gx[k], gdx);
         gdy = fmaf(gY, Gy[k], gdy);
@@ -443,7 +471,7 @@ cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, cons
                                                             cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
                                                             final_T, n_contrib, dL_dcolor, dsplat);
     if (s.n > 0)
-        preprocess_backward_kernel<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(
+        preprocess_backward_kernel<<<(unsigned)((s.n + kPreBackThreads - 1) / kPreBackThreads), kPreBackThreads, 0, st>>>(
             s.means, s.log_scales, reinterpret_cast<const float4 *>(s.quats), s.opacity_logits, s.sh, s.n,
             s.sh_degree, cam, splats, dsplat, g.dmeans, g.dlog_scales, g.dquats, g.dopacity_logits, g.dsh);
     return cudaGetLastError();

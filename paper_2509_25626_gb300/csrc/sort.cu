@@ -240,34 +240,45 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
     for (int i = threadIdx.x; i < (kThreads / 32) * 4 * kBins; i += kThreads) (&s_hist[0][0][0])[i] = 0;
     for (int i = threadIdx.x; i < kMaxTilePasses * (kBins + 1); i += kThreads) (&s_tdiff[0][0])[i] = 0;
     const uint32_t blk = dynamic_block(&ws.hdr->tile_ctr[kCtrCompact], &s_slot);
-    const int64_t base = (int64_t)blk * kSortTileItems + (int64_t)threadIdx.x * kIpt;  // 16 consecutive per thread
+    // warp w reads elements [w*512, w*512 + 512) of the block, lane-strided, so
+    // every load instruction covers 512 contiguous bytes
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const int64_t wbase = (int64_t)blk * kSortTileItems + (int64_t)warp * (kIpt * 32) + lane;
     // (depth, tiles, rect lo, rect hi): the dense copy after the n records
     const uint4 *__restrict__ sort_in = reinterpret_cast<const uint4 *>(splats + n);
     uint4 r4[kIpt];
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
-        const int64_t i = base + k;
+        const int64_t i = wbase + k * 32;
         r4[k] = i < n ? __ldg(sort_in + i) : make_uint4(0u, 0u, 0u, 0u);
     }
-    uint32_t vis = 0;  // bit k: element base + k is visible
+    // visible elements in element order: per k a ballot over the warp, then
+    // warps in order, then blocks in order
+    unsigned bal[kIpt];
+    uint32_t wcount = 0;
 #pragma unroll
-    for (int k = 0; k < kIpt; ++k) vis |= (r4[k].y != 0u ? 1u : 0u) << k;
+    for (int k = 0; k < kIpt; ++k) {
+        bal[k] = __ballot_sync(0xffffffffu, r4[k].y != 0u);
+        wcount += (uint32_t)__popc(bal[k]);
+    }
     uint32_t total;
-    const uint32_t ex = block_exclusive_scan((uint32_t)__popc(vis), scratch, &total);
+    const uint32_t wex = block_exclusive_scan(lane == 0 ? wcount : 0u, scratch, &total);
+    const uint32_t wexcl = __shfl_sync(0xffffffffu, wex, 0);  // visible elements of the earlier warps
     const uint64_t excl = prefix_from_aggregates(ws.scan_state[0], blk, total, ws.hdr, scratch64);
-    uint32_t pos = (uint32_t)excl + ex;
-    const unsigned warp = threadIdx.x >> 5;
+    uint32_t pos = (uint32_t)excl + wexcl;
+    const unsigned lt = lanemask_lt();
     const bool small_grid = tl.x_bytes == 1 && tl.y_bytes <= 1;
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const uint32_t d = r4[k].x;
-        if ((vis >> k) & 1u) {
-            const uint32_t g = (uint32_t)(base + k);
-            ws.dkey[0][pos] = d;  // positive float: uint order = float order
-            ws.dval[0][pos] = g;
+        const bool vis = (bal[k] >> lane) & 1u;
+        if (vis) {
+            const uint32_t g = (uint32_t)(wbase + k * 32);
+            const uint32_t q = pos + (uint32_t)__popc(bal[k] & lt);
+            ws.dkey[0][q] = d;  // positive float: uint order = float order
+            ws.dval[0][q] = g;
             ws.depthv[g] = d;
             ws.rectv[g] = make_uint2(r4[k].z, r4[k].w);
-            ++pos;
             atomicAdd(&s_hist[warp][0][d & 0xffu], 1u);
             atomicAdd(&s_hist[warp][1][(d >> 8) & 0xffu], 1u);
             const uint32_t x0 = r4[k].z & 0xffffu, y0 = r4[k].z >> 16, x1 = r4[k].w & 0xffffu, y1 = r4[k].w >> 16;
@@ -282,9 +293,10 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
                 add_rect_digits(s_tdiff, tl, x0, x1, y0, y1, 1u);
             }
         }
+        pos += (uint32_t)__popc(bal[k]);
         // the two high bytes take few distinct values: aggregate them per warp
-        warp_hist_add(s_hist[warp][2], ((vis >> k) & 1u) ? ((d >> 16) & 0xffu) : 0xffffffffu);
-        warp_hist_add(s_hist[warp][3], ((vis >> k) & 1u) ? (d >> 24) : 0xffffffffu);
+        warp_hist_add(s_hist[warp][2], vis ? ((d >> 16) & 0xffu) : 0xffffffffu);
+        warp_hist_add(s_hist[warp][3], vis ? (d >> 24) : 0xffffffffu);
     }
     if (blk == gridDim.x - 1 && threadIdx.x == 0) ws.hdr->nvis = (uint32_t)(excl + total);
     __syncthreads();

@@ -473,24 +473,41 @@ __global__ void __launch_bounds__(kThreads, 3) offsets_kernel(SortWs ws, uint64_
     const uint32_t nblocks = (n + kSortTileItems - 1) / kSortTileItems;
     const uint32_t blk = dynamic_block(&ws.hdr->tile_ctr[kCtrOffsets], &s_slot);
     if (blk >= nblocks) return;
-    const uint32_t base = blk * kSortTileItems + threadIdx.x * kIpt;
+    // warp w holds splats [w*512, w*512 + 512) of the block, lane-strided
+    // (coalesced reads of the depth-sorted ids); element order is (k, lane)
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t wbase = blk * kSortTileItems + warp * (kIpt * 32) + lane;
     uint32_t tt[kIpt];
-    uint64_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
-        const uint32_t i = base + k;
+        const uint32_t i = wbase + k * 32;
         const uint2 rc = i < n ? ws.rectv[ws.dval[0][i]] : make_uint2(0u, 0u);
         tt[k] = ((rc.y & 0xffffu) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.x >> 16));
-        sum += tt[k];
+    }
+    // per k: this lane's exclusive prefix within the warp's 32 elements, and
+    // the warp's running total before k
+    uint64_t lane_ex[kIpt];
+    uint64_t wsum = 0;
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) {
+        uint64_t inc = tt[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (unsigned)o) inc += x;
+        }
+        lane_ex[k] = wsum + inc - tt[k];
+        wsum += __shfl_sync(0xffffffffu, inc, 31);
     }
     uint64_t total;
-    const uint64_t ex = block_exclusive_scan64(sum, scratch, &total);
+    const uint64_t wex = block_exclusive_scan64(lane == 0 ? wsum : 0ull, scratch, &total);
+    const uint64_t wexcl = __shfl_sync(0xffffffffu, wex, 0);  // instances of the earlier warps
     const uint64_t excl = prefix_from_aggregates(ws.scan_state[1], blk, total, ws.hdr, scratch);
-    uint64_t pos = excl + ex;
     const uint64_t nsweep = (m_cap + kSortTileItems - 1) / kSortTileItems;
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
-        const uint32_t i = base + k;
+        const uint32_t i = wbase + k * 32;
+        const uint64_t pos = excl + wexcl + lane_ex[k];
         if (i < n) {
             ws.offs[i] = (uint32_t)(pos < 0xffffffffull ? pos : 0xffffffffull);
             // tile-pass blocks whose first instance falls inside this splat's run
@@ -507,7 +524,6 @@ __global__ void __launch_bounds__(kThreads, 3) offsets_kernel(SortWs ws, uint64_
                 add_rect_digits(diff, tl, x0 + part, x1, y0 + rows, y0 + rows + 1u, 0xffffffffu);  // a partial row
             }
         }
-        pos += tt[k];
     }
     if (blk == nblocks - 1 && threadIdx.x == 0) {
         const uint64_t m = excl + total;

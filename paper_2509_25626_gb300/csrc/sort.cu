@@ -40,7 +40,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kIpt = kSortTileItems / kThreads;  // 16 items per thread
-constexpr int kDepthIpt = kDepthItems / kThreads;  // items per thread in the depth passes
+// Threads per block of the radix passes over arrays (4096 elements each).
+constexpr int kSweepThreads = 256;  // 512 measured slower
 // Predecessors read per round trip of the depth passes' look-back (wider
 // windows measured slower).
 constexpr int kDepthWin = 8;
@@ -321,25 +322,28 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
 // that loads values from memory keeps them out of registers while ranking.
 // kFinal: write the full 64-bit key (row-major tile id << 32 | depth bits of
 // the value), the tile id rebuilt from the byte-aligned key.
-template <int IPT>
+// NT threads per block (256 or 512), kSortTileItems / NT elements each.
+template <int NT>
 struct SweepSmemT {
-    uint32_t keys[IPT * kThreads];
-    uint32_t vals[IPT * kThreads];
-    uint32_t wcnt[kThreads / 32][kBins];
+    uint32_t keys[kSortTileItems];
+    uint32_t vals[kSortTileItems];
+    uint32_t wcnt[NT / 32][kBins];
     uint32_t base[kBins];
     uint32_t dstart[kBins];
     uint32_t scratch[33];
 };
-using SweepSmem = SweepSmemT<kIpt>;
+using SweepSmem = SweepSmemT<kThreads>;
 
-template <bool kFinal, int IPT, int WIN, typename ValFn>
-__device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t (&key)[IPT], ValFn val,
+template <bool kFinal, int NT, int WIN, typename ValFn>
+__device__ __forceinline__ void rank_scatter(SweepSmemT<NT> &sm, const uint32_t (&key)[kSortTileItems / NT], ValFn val,
                                              uint32_t start, uint32_t n, uint32_t blk, int shift,
                                              uint32_t digit_total, uint64_t *__restrict__ state, SortHeader *hdr,
                                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                              uint64_t *__restrict__ kout64, const uint32_t *__restrict__ depthv,
                                              int shift_y, uint32_t tiles_x) {
+    constexpr int IPT = kSortTileItems / NT;
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    const bool digit_thread = t < (unsigned)kBins;  // thread t < 256 owns digit t
     const unsigned lt = lanemask_lt();
     const uint32_t wbase = start + warp * (IPT * 32) + lane;
     // stable warp-local ranking (sm.wcnt is zero on entry)
@@ -359,17 +363,22 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t
     __syncthreads();
     // digit t: prefix over warps, this block's count, and its start in the block
     uint32_t cnt = 0;
+    if (digit_thread) {
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-        const uint32_t c = sm.wcnt[w][t];
-        sm.wcnt[w][t] = cnt;
-        cnt += c;
+        for (int w = 0; w < NT / 32; ++w) {
+            const uint32_t c = sm.wcnt[w][t];
+            sm.wcnt[w][t] = cnt;
+            cnt += c;
+        }
     }
     uint32_t tot;
-    sm.dstart[t] = block_exclusive_scan(cnt, sm.scratch, &tot);
-    const uint32_t dbase = block_exclusive_scan(digit_total, sm.scratch, &tot);
-    const uint64_t excl = look_back<WIN>(state + t, blk, kBins, cnt, hdr);
-    sm.base[t] = dbase + (uint32_t)excl;
+    const uint32_t dst = block_exclusive_scan(cnt, sm.scratch, &tot);
+    const uint32_t dbase = block_exclusive_scan(digit_thread ? digit_total : 0u, sm.scratch, &tot);
+    if (digit_thread) {
+        sm.dstart[t] = dst;
+        const uint64_t excl = look_back<WIN>(state + t, blk, kBins, cnt, hdr);
+        sm.base[t] = dbase + (uint32_t)excl;
+    }
     __syncthreads();
     uint32_t vals[IPT];
 #pragma unroll
@@ -385,14 +394,14 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t
         }
     }
     __syncthreads();
-    const uint32_t cnt_blk = min((uint32_t)(IPT * kThreads), n - start);
+    const uint32_t cnt_blk = min((uint32_t)kSortTileItems, n - start);
     constexpr int kHalf = IPT / 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t gp[kHalf], kk[kHalf], vv[kHalf];
 #pragma unroll
         for (int k = 0; k < kHalf; ++k) {
-            const uint32_t j = t + (h * kHalf + k) * kThreads;
+            const uint32_t j = t + (h * kHalf + k) * NT;
             gp[k] = 0xffffffffu;
             kk[k] = vv[k] = 0u;
             if (j < cnt_blk) {
@@ -424,11 +433,11 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<IPT> &sm, const uint32_t
     }
 }
 
-// One pass over (key, value) arrays in device memory, IPT x 256 elements per
-// block.  diff_hist: the digit totals are given as a difference array (the
-// tile passes).
-template <bool kFinal, int IPT, int WIN>
-__global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(const uint32_t *__restrict__ kin,
+// One pass over (key, value) arrays in device memory, kSortTileItems
+// elements per block of NT threads.  diff_hist: the digit totals are given
+// as a difference array (the tile passes).
+template <bool kFinal, int NT, int WIN>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) onesweep_kernel(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                             uint64_t *__restrict__ kout64,
@@ -438,27 +447,27 @@ __global__ void __launch_bounds__(kThreads, IPT <= 8 ? 4 : 3) onesweep_kernel(co
                                                             uint64_t *__restrict__ state, uint32_t *__restrict__ ctr,
                                                             SortHeader *__restrict__ hdr, int shift_y,
                                                             uint32_t tiles_x) {
-    __shared__ SweepSmemT<IPT> sm;
+    constexpr int IPT = kSortTileItems / NT;
+    __shared__ SweepSmemT<NT> sm;
     __shared__ uint32_t s_slot;
     const uint32_t n = *count_ptr;
-    const uint32_t nblocks = (n + IPT * kThreads - 1) / (IPT * kThreads);
+    const uint32_t nblocks = (n + kSortTileItems - 1) / kSortTileItems;
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) sm.wcnt[w][t] = 0;
+    for (int i = (int)t; i < (NT / 32) * kBins; i += NT) (&sm.wcnt[0][0])[i] = 0;
     const uint32_t blk = dynamic_block(ctr, &s_slot);  // contains __syncthreads
     if (blk >= nblocks) return;                        // uniform over the block
-    const uint32_t start = blk * (IPT * kThreads);
+    const uint32_t start = blk * kSortTileItems;
     const uint32_t wbase = start + warp * (IPT * 32) + lane;
     uint32_t key[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) key[k] = (wbase + k * 32 < n) ? kin[wbase + k * 32] : 0u;
-    uint32_t dt = digit_total[t];
+    uint32_t dt = t < (unsigned)kBins ? digit_total[t] : 0u;
     if (diff_hist) {  // uniform
         uint32_t tot;
         dt += block_exclusive_scan(dt, sm.scratch, &tot);
     }
     auto val = [&](int k) { return (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u; };
-    rank_scatter<kFinal, IPT, WIN>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
+    rank_scatter<kFinal, NT, WIN>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
                                    shift_y, tiles_x);
 }
 
@@ -639,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
     __syncthreads();
-    rank_scatter<kFinal, kIpt, 8>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+    rank_scatter<kFinal, kThreads, 8>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
                          ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
 }
 
@@ -674,7 +683,7 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
     const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
     for (int p = 0; p < 4; ++p)
-        onesweep_kernel<false, kDepthIpt, kDepthWin><<<nbd, kThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+        onesweep_kernel<false, kSweepThreads, kDepthWin><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
                                                          ws.hist_depth + kBins * p, false, ws.depth_state[p],
                                                          &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
@@ -703,12 +712,12 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
         for (int p = 1; p < passes; ++p) {
             const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
             if (p == passes - 1)
-                onesweep_kernel<true, kIpt, 8><<<nb, kThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
+                onesweep_kernel<true, kSweepThreads, 8><<<nb, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
                                                                 &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
                                                                 &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
                                                                 tx);
             else
-                onesweep_kernel<false, kIpt, 8><<<nb, kThreads, 0, st>>>(
+                onesweep_kernel<false, kSweepThreads, 8><<<nb, kSweepThreads, 0, st>>>(
                     buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
                     true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }

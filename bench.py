@@ -416,9 +416,29 @@ def main():
                     tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
     )
     # kernels per frame: preprocess; compact, 4 depth radix passes, offsets,
-    # duplicate, one radix pass per 8 bits of tile id, ranges; render
-    tb = max(0, math.ceil(math.log2(T))) if T > 1 else 0
-    launches_per_frame = 1 + (1 + 4 + 1 + 1 + max(1, (tb + 7) // 8) + 1) + 1
+    # duplicate fused with the first tile pass, one more pass per further
+    # byte of the tile key (a byte of tx, then of ty), ranges; render
+    tiles_x, tiles_y = (W + 15) // 16, (H + 15) // 16
+    key_bytes = lambda c: 0 if c <= 1 else (1 if c <= 256 else 2)
+    tile_passes = max(1, key_bytes(tiles_x)) + key_bytes(tiles_y)
+    launches_per_frame = 1 + (1 + 4 + 1 + tile_passes + 1) + 1
+
+    # frame roofline: each step's floor (HBM bytes / measured HBM for the
+    # preprocess and the sort, the FP32 issue floor for the render) summed,
+    # against the measured frame time (frames one at a time)
+    nvis = vis[0]
+    sort_bytes = (n * 16 + nvis * 12                     # compaction: sort inputs in; keys, ids, depth out
+                  + 4 * nvis * 16                        # four depth passes: (key, id) in and out
+                  + nvis * 12                            # offsets: ids, rectangles, offsets
+                  + ms_mean * 8                          # duplicate + first tile pass: (tile, id) out
+                  + ms_mean * 20                         # last tile pass: 8 B in, 12 B out
+                  + T * 8)                               # ranges
+    floors = dict(preprocess_ms=pre_bytes / (peaks["hbm_gbs"] * 1e6),
+                  sort_ms=sort_bytes / (peaks["hbm_gbs"] * 1e6),
+                  render_ms=evals_mean * FLOP_PER_EVAL / (fp32_peak * 1e9))
+    frame_roofline = dict(floor_ms=sum(floors.values()), frame_ms=1000.0 / serial_fps,
+                          frac=sum(floors.values()) / (1000.0 / serial_fps), **floors,
+                          sort_bytes=sort_bytes)
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -450,7 +470,8 @@ def main():
                         m_cap=m_cap, parallelism=f"replicas{world}", frames_in_flight=F,
                         serial_frames_per_s=serial_fps,
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
-            roofline=roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e, serving=serving, multiview=multiview,
+            roofline=roofline, frame_roofline=frame_roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
+            serving=serving, multiview=multiview,
             backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,
             peaks_src=peaks["src"],

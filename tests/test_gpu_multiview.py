@@ -50,3 +50,43 @@ def test_multiview_batch_equals_single_views():
     for (cam, sp, vals, ranges, ref), out in zip(views, outs):
         for a, b in zip(out, ref):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n_jobs", [64, 70])
+def test_batch_job_table_sizes(n_jobs):
+    """A batch of many small jobs (mixed sizes and backgrounds): up to 64 the
+    kernel keeps the job table in shared memory, beyond it reads each item's
+    job from device memory; both give every job its own gs_render output."""
+    sc = slab_scene(20_000, seed=5)
+    st = gs.SceneTensors.from_scene(sc, "cuda")
+    sizes = [(48, 32), (33, 17), (64, 64), (16, 16), (80, 45)]
+    jobs = []
+    for k in range(n_jobs):
+        w, h = sizes[k % len(sizes)]
+        cam = orbit_camera(k % 8, 8, 4.0, w, h, arc=np.radians(40.0))
+        bg = (0.1 * (k % 3), 0.2, 0.05 * (k % 5))
+        sp = gs.preprocess(st, cam)
+        _, vals, ranges, m, _ = gs.sort(sp, st.n, cam, 1 << 20)
+        ref = gs.render(sp, vals, ranges, cam, bg)
+        jobs.append((cam, bg, sp, vals, ranges, ref, tuple(torch.empty_like(t) for t in ref)))
+    srv = S.Server({}, max_batch=n_jobs)
+
+    class _Req:
+        def __init__(self, cam, bg):
+            self.cam, self.bg = cam, bg
+
+    class _Slot:
+        def __init__(self, sp, vals, ranges, out, cam):
+            self.splats, self.vals, self.ranges = sp, vals, ranges
+            self.image, self.final_T, self.n_contrib = out
+            self.tiles = gs.num_tiles(cam)
+
+    srv._write_desc([(_Req(c, bg), _Slot(sp, v, r, o, c)) for c, bg, sp, v, r, _, o in jobs])
+    srv.desc_dev.copy_(srv.desc_host)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
+                                    ctypes.c_void_p(srv.counter.data_ptr()), 0, stream), "gs_render_batch")
+    torch.cuda.synchronize()
+    for c, bg, sp, v, r, ref, out in jobs:
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b)

@@ -255,17 +255,16 @@ def main():
 
     # evaluations per pose (untimed), the render's work count, and the
     # per-tile block cycles (load balance)
-    evals, tile_stats = [], []
+    evals, tile_stats, vis, front = [], [], [], []
     for cam in cams:
         gs.preprocess(st, cam, r.splats)
+        words = r.splats.view(torch.int32)[:n]
+        vis.append(int((words[:, 13] > 0).sum().item()))  # tiles_touched > 0
+        front.append(int((r.splats[:n, 12] > 0.2).sum().item()))  # in front of the near plane
         gs.sort(r.splats, n, cam, m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
         _, _, _, ne, cyc = gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)
         evals.append(int(ne.to(torch.int64).sum().item()))
         tile_stats.append(tile_cycle_stats(cyc))
-    vis = []
-    for cam in cams[:1]:
-        gs.preprocess(st, cam, r.splats)
-        vis.append(int((r.splats.view(torch.int32)[:n, 13] > 0).sum().item()))  # tiles_touched
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: rank_pose(k, world, rank, P)
@@ -392,7 +391,12 @@ def main():
     evals_mean = statistics.mean(evals[p] for p in used)
     ms_mean = statistics.mean(ms[p] for p in used)
     render_tflops = evals_mean * FLOP_PER_EVAL / (rend_ms / 1000.0) / 1e12
-    pre_bytes = n * (236 + 64 + 16)  # scene in; record and dense sort inputs out
+    # preprocess bytes: every Gaussian's mean; scales and rotation of those
+    # in front of the near plane; opacity and SH of the visible ones (culled
+    # Gaussians need neither); the record and the dense sort inputs out
+    front_mean = statistics.mean(front[p] for p in used)
+    vis_mean = statistics.mean(vis[p] for p in used)
+    pre_bytes = n * 12 + front_mean * 28 + vis_mean * (4 + 192) + n * (64 + 16)
     pre_gbs = pre_bytes / (pre_ms / 1000.0) / 1e9
     traffic = None
     try:
@@ -426,7 +430,7 @@ def main():
     # frame roofline: each step's floor (HBM bytes / measured HBM for the
     # preprocess and the sort, the FP32 issue floor for the render) summed,
     # against the measured frame time (frames one at a time)
-    nvis = vis[0]
+    nvis = vis_mean
     sort_bytes = (n * 16 + nvis * 12                     # compaction: sort inputs in; keys, ids, depth out
                   + 4 * nvis * 16                        # four depth passes: (key, id) in and out
                   + nvis * 12                            # offsets: ids, rectangles, offsets

@@ -66,12 +66,44 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     }
     const float tx = fmaf(V[2], mz, fmaf(V[1], my, fmaf(V[0], mx, V[3])));
     const float ty = fmaf(V[6], mz, fmaf(V[5], my, fmaf(V[4], mx, V[7])));
+    const float s0 = expf(log_scales[3 * g]), s1 = expf(log_scales[3 * g + 1]), s2 = expf(log_scales[3 * g + 2]);
+
+    // Early, conservative frustum cull from the mean and the largest scale:
+    // lambda_max(Sigma') <= trace(T T^T) max(s)^2 + 0.3 with T = J W (the
+    // Frobenius norm bounds the spectral one), and the radius test below adds
+    // at most sqrt(0.1) to lambda, so a Gaussian whose mean lies farther than
+    // that bound outside the image has an empty rectangle.
+    // Survivors are likely visible: start fetching their SH into L2 now, so
+    // the loads after the covariance arithmetic find it there.
+    {
+        const float iz = 1.0f / z;
+        const float lx = kFrustumSlack * cam.tan_fovx, ly = kFrustumSlack * cam.tan_fovy;
+        const float cx_ = fminf(lx, fmaxf(-lx, tx * iz)), cy_ = fminf(ly, fmaxf(-ly, ty * iz));
+        const float fxz = cam.fx * iz, fyz = cam.fy * iz;
+        const float smax = fmaxf(s0, fmaxf(s1, s2));
+        float tr = 0.f;  // |T row 0|^2 + |T row 1|^2, rows fx/z (W0 - cx W2), fy/z (W1 - cy W2)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float a = fxz * fmaf(-cx_, V[8 + j], V[j]), b = fyz * fmaf(-cy_, V[8 + j], V[4 + j]);
+            tr = fmaf(a, a, fmaf(b, b, tr));
+        }
+        const float r_ub = 3.0f * sqrtf(fmaf(tr, smax * smax, kDilation + 0.3163f)) * 1.01f + 2.0f;
+        const float px_ = fmaf(cam.fx, tx * iz, cam.cx), py_ = fmaf(cam.fy, ty * iz, cam.cy);
+        const float wimg = (float)(cam.tiles_x * kTile), himg = (float)(cam.tiles_y * kTile);
+        if (px_ + r_ub < 0.f || py_ + r_ub < 0.f || px_ - r_ub > wimg || py_ - r_ub > himg) {
+            write_culled(out + g, sort_in + g, z);
+            return;
+        }
+        const char *shp = reinterpret_cast<const char *>(sh + 12 * g);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shp));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shp + 64));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(shp + 128));
+    }
 
     // R(q) S: rotation from the normalised quaternion, columns scaled.
     float4 q = quats[g];
     const float qinv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float qw = q.x * qinv, qx = q.y * qinv, qy = q.z * qinv, qz = q.w * qinv;
-    const float s0 = expf(log_scales[3 * g]), s1 = expf(log_scales[3 * g + 1]), s2 = expf(log_scales[3 * g + 2]);
     float M[3][3];
     M[0][0] = (1.f - 2.f * (qy * qy + qz * qz)) * s0;
     M[0][1] = 2.f * (qx * qy - qw * qz) * s1;

@@ -322,11 +322,11 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
 // that loads values from memory keeps them out of registers while ranking.
 // kFinal: write the full 64-bit key (row-major tile id << 32 | depth bits of
 // the value), the tile id rebuilt from the byte-aligned key.
-// NT threads per block (256 or 512), kSortTileItems / NT elements each.
-template <int NT>
+// NT threads per block, ITEMS elements per block (ITEMS / NT each).
+template <int NT, int ITEMS = kSortTileItems>
 struct SweepSmemT {
-    uint32_t keys[kSortTileItems];
-    uint32_t vals[kSortTileItems];
+    uint32_t keys[ITEMS];
+    uint32_t vals[ITEMS];
     uint32_t wcnt[NT / 32][kBins];
     uint32_t base[kBins];
     uint32_t dstart[kBins];
@@ -334,14 +334,14 @@ struct SweepSmemT {
 };
 using SweepSmem = SweepSmemT<kThreads>;
 
-template <bool kFinal, int NT, int WIN, typename ValFn>
-__device__ __forceinline__ void rank_scatter(SweepSmemT<NT> &sm, const uint32_t (&key)[kSortTileItems / NT], ValFn val,
+template <bool kFinal, int NT, int WIN, int ITEMS, typename ValFn>
+__device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const uint32_t (&key)[ITEMS / NT], ValFn val,
                                              uint32_t start, uint32_t n, uint32_t blk, int shift,
                                              uint32_t digit_total, uint64_t *__restrict__ state, SortHeader *hdr,
                                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                              uint64_t *__restrict__ kout64, const uint32_t *__restrict__ depthv,
                                              int shift_y, uint32_t tiles_x) {
-    constexpr int IPT = kSortTileItems / NT;
+    constexpr int IPT = ITEMS / NT;
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const bool digit_thread = t < (unsigned)kBins;  // thread t < 256 owns digit t
     const unsigned lt = lanemask_lt();
@@ -394,7 +394,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT> &sm, const uint32_t 
         }
     }
     __syncthreads();
-    const uint32_t cnt_blk = min((uint32_t)kSortTileItems, n - start);
+    const uint32_t cnt_blk = min((uint32_t)ITEMS, n - start);
     constexpr int kHalf = IPT / 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -433,11 +433,11 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT> &sm, const uint32_t 
     }
 }
 
-// One pass over (key, value) arrays in device memory, kSortTileItems
-// elements per block of NT threads.  diff_hist: the digit totals are given
-// as a difference array (the tile passes).
-template <bool kFinal, int NT, int WIN>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) onesweep_kernel(const uint32_t *__restrict__ kin,
+// One pass over (key, value) arrays in device memory, ITEMS elements per
+// block of NT threads.  diff_hist: the digit totals are given as a
+// difference array (the tile passes).
+template <bool kFinal, int NT, int WIN, int ITEMS>
+__global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3)) onesweep_kernel(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                             uint64_t *__restrict__ kout64,
@@ -447,16 +447,16 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) onesweep_kernel(const u
                                                             uint64_t *__restrict__ state, uint32_t *__restrict__ ctr,
                                                             SortHeader *__restrict__ hdr, int shift_y,
                                                             uint32_t tiles_x) {
-    constexpr int IPT = kSortTileItems / NT;
-    __shared__ SweepSmemT<NT> sm;
+    constexpr int IPT = ITEMS / NT;
+    __shared__ SweepSmemT<NT, ITEMS> sm;
     __shared__ uint32_t s_slot;
     const uint32_t n = *count_ptr;
-    const uint32_t nblocks = (n + kSortTileItems - 1) / kSortTileItems;
+    const uint32_t nblocks = (n + ITEMS - 1) / ITEMS;
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     for (int i = (int)t; i < (NT / 32) * kBins; i += NT) (&sm.wcnt[0][0])[i] = 0;
     const uint32_t blk = dynamic_block(ctr, &s_slot);  // contains __syncthreads
     if (blk >= nblocks) return;                        // uniform over the block
-    const uint32_t start = blk * kSortTileItems;
+    const uint32_t start = blk * ITEMS;
     const uint32_t wbase = start + warp * (IPT * 32) + lane;
     uint32_t key[IPT];
 #pragma unroll
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) onesweep_kernel(const u
         dt += block_exclusive_scan(dt, sm.scratch, &tot);
     }
     auto val = [&](int k) { return (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u; };
-    rank_scatter<kFinal, NT, WIN>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
+    rank_scatter<kFinal, NT, WIN, ITEMS>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
                                    shift_y, tiles_x);
 }
 
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
     __syncthreads();
-    rank_scatter<kFinal, kThreads, 8>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+    rank_scatter<kFinal, kThreads, 8, kSortTileItems>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
                          ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
 }
 
@@ -683,7 +683,7 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
     const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
     for (int p = 0; p < 4; ++p)
-        onesweep_kernel<false, kSweepThreads, kDepthWin><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+        onesweep_kernel<false, kSweepThreads, kDepthWin, kSortTileItems><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
                                                          ws.hist_depth + kBins * p, false, ws.depth_state[p],
                                                          &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
@@ -704,6 +704,7 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
         auto buf_k = [&](int k) { return ((passes - 1 - k) % 2 == 0) ? ws.tkey : scratch_k; };
         auto buf_v = [&](int k) { return ((passes - 1 - k) % 2 == 0) ? ws.tval : scratch_v; };
         const uint32_t nb = (uint32_t)sort_blocks_for(m_cap);
+        const uint32_t nbt = (uint32_t)tile_pass_blocks_for(m_cap);
         const uint32_t tx = (uint32_t)tiles_x;
         if (passes == 1)
             dup_sweep_kernel<true><<<nb, kThreads, 0, st>>>(ws, tl, tx, nullptr, vals, keys);
@@ -712,12 +713,12 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
         for (int p = 1; p < passes; ++p) {
             const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
             if (p == passes - 1)
-                onesweep_kernel<true, kSweepThreads, 8><<<nb, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
+                onesweep_kernel<true, kSweepThreads, 8, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
                                                                 &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
                                                                 &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
                                                                 tx);
             else
-                onesweep_kernel<false, kSweepThreads, 8><<<nb, kSweepThreads, 0, st>>>(
+                onesweep_kernel<false, kSweepThreads, 8, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(
                     buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
                     true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }

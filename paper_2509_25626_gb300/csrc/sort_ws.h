@@ -8,6 +8,7 @@ namespace gs {
 
 constexpr int kSortTileItems = 4096;   // elements per block in the look-back scans and tile radix passes
 constexpr int kDepthItems = 4096;      // elements per block in the depth radix passes
+constexpr int kTilePassItems = 4096;   // elements per block in the tile passes after the first (2048 measured slower)
 constexpr int kMaxTilePasses = 4;      // 8-bit digits of a 32-bit tile id
 
 // Device-side counters of one gs_sort call (first 256 bytes of the workspace).
@@ -40,6 +41,7 @@ struct SortWs {
 
 inline uint64_t sort_blocks_for(uint64_t count) { return (count + kSortTileItems - 1) / kSortTileItems; }
 inline uint64_t depth_blocks_for(uint64_t count) { return (count + kDepthItems - 1) / kDepthItems; }
+inline uint64_t tile_pass_blocks_for(uint64_t count) { return (count + kTilePassItems - 1) / kTilePassItems; }
 
 inline int tile_bits_of(uint64_t num_tiles) {
     int b = 0;
@@ -95,13 +97,14 @@ inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, uint64_t num_t
     };
     const uint64_t nn = (uint64_t)(n > 0 ? n : 0), mc = (uint64_t)(m_cap > 0 ? m_cap : 0);
     const uint64_t bn = sort_blocks_for(nn) + 1, bm = sort_blocks_for(mc) + 1, bd = depth_blocks_for(nn) + 1;
+    const uint64_t bt = tile_pass_blocks_for(mc) + 1;
     const int passes = tile_passes_bound(num_tiles);
     SortWs w{};
     w.hdr = reinterpret_cast<SortHeader *>(take(sizeof(SortHeader)));
     for (int i = 0; i < 2; ++i) w.scan_state[i] = reinterpret_cast<uint64_t *>(take(8 * bn));
     for (int i = 0; i < 4; ++i) w.depth_state[i] = reinterpret_cast<uint64_t *>(take(8 * 256 * bd));
-    for (int i = 0; i < kMaxTilePasses; ++i)
-        w.tile_state[i] = reinterpret_cast<uint64_t *>(i < passes ? take(8 * 256 * bm) : nullptr);
+    for (int i = 0; i < kMaxTilePasses; ++i)  // pass 0 (fused with duplication) uses 4096-element blocks
+        w.tile_state[i] = reinterpret_cast<uint64_t *>(i < passes ? take(8 * 256 * (i == 0 ? bm : bt)) : nullptr);
     w.hist_depth = reinterpret_cast<uint32_t *>(take(4 * 4 * 256));
     w.hist_tile = reinterpret_cast<uint32_t *>(take(4 * kMaxTilePasses * 257));
     w.zero_bytes = off;

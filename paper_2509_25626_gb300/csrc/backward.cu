@@ -66,15 +66,18 @@ struct PixelBack {
 };
 
 // One pixel's contribution for one splat at list position `pos`; adds to g[9].
+// arg = log2 alpha before the clamp, computed exactly as the forward does,
+// so the skip decision (taken on it, as in the forward) is the forward's.
+// inv_o = 1 / opacity.
 __device__ __forceinline__ void back_pixel(PixelBack &p, uint32_t pos, float u, float v, float dx, float dy,
                                            float arg, float w00, float w01, float w11, float r, float g, float b,
-                                           float o, float *acc) {
+                                           float inv_o, float *acc) {
     if (pos > p.last) return;
+    if (!(arg >= -kLog2_255)) return;  // alpha < 1/255: skipped by the forward
     const float raw = ex2_approx(arg);
     const float alpha = fminf(kAlphaMax, raw);
-    if (alpha < kAlphaMin) return;
-    const float om = 1.0f - alpha;
-    const float Tb = p.T / om;  // transmittance in front of this splat
+    const float om = 1.0f - alpha;  // >= 0.01
+    const float Tb = __fdividef(p.T, om);  // transmittance in front of this splat
     const float wgt = alpha * Tb;
     acc[6] = fmaf(wgt, p.g0, acc[6]);
     acc[7] = fmaf(wgt, p.g1, acc[7]);
@@ -86,7 +89,7 @@ __device__ __forceinline__ void back_pixel(PixelBack &p, uint32_t pos, float u, 
     p.T = Tb;
     if (raw > kAlphaMax) return;  // clamped: alpha does not depend on o or power
     // alpha = o G, G = exp(power): dL/do = dL/dalpha G, dL/dpower = dL/dalpha alpha
-    acc[5] = fmaf(dL_dalpha, raw / o, acc[5]);
+    acc[5] = fmaf(dL_dalpha, raw * inv_o, acc[5]);
     const float gp = dL_dalpha * alpha;
     // Q d = 2 ln2 W^T (u, v): d power / d mean = -Q d
     const float qx = 2.0f * kLn2 * (w00 * u), qy = 2.0f * kLn2 * fmaf(w01, u, w11 * v);
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
                 s_a[k] = StagedA{a.x, a.y, a.z, a.w};
                 s_b[k] = StagedB{b.x, b.y, b.z, b.w};
                 s_c[k] = c.x;
-                s_o[k] = ex2_approx(b.y);
+                s_o[k] = ex2_approx(-b.y);  // 1 / opacity
                 s_gid[k] = gid;
                 const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
                 const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
             if (pos > wlast) continue;  // warp-uniform: no pixel of this warp reached it
             const StagedA sa = s_a[j];
             const StagedB sb = s_b[j];
-            const float b = s_c[j], o = s_o[j];
+            const float b = s_c[j], inv_o = s_o[j];
             const float dy = sa.y - pyf;
             const float dx0 = sa.x - pxf, dx1 = dx0 - 1.0f;
             const float t = sa.w01 * dy;
@@ -201,8 +204,8 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
             float acc[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-            back_pixel(p0, pos, u0, v, dx0, dy, fmaf(-u0, u0, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, o, acc);
-            back_pixel(p1, pos, u1, v, dx1, dy, fmaf(-u1, u1, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, o, acc);
+            back_pixel(p0, pos, u0, v, dx0, dy, fmaf(-u0, u0, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, inv_o, acc);
+            back_pixel(p1, pos, u1, v, dx1, dy, fmaf(-u1, u1, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, inv_o, acc);
             const bool any = acc[6] != 0.f || acc[7] != 0.f || acc[8] != 0.f || acc[5] != 0.f || acc[0] != 0.f;
             if (__any_sync(0xffffffffu, any)) {
                 const float sum = warp_sum16(acc, lane);

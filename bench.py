@@ -336,7 +336,7 @@ def main():
     # end to end through the public API: scene from pinned host memory each
     # step, image back to pinned host memory; FramePipeline overlaps the
     # upload of frame k+1 with the render of frame k
-    e2e = None
+    e2e = e2e_resident = None
     if not args.no_e2e:
         host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in scene.arrays()]
         h2d = sum(h.numel() * h.element_size() for h in host)
@@ -361,6 +361,39 @@ def main():
                    d2h_bytes_per_step=d2h, h2d_gbs=h2d * args.steps / (te / 1e3) / 1e9,
                    note="FramePipeline: uploads of frame k+1 overlap the render of frame k")
         del pipe
+        # resident scene (a served model): per frame only the camera goes in
+        # (kernel parameters) and the image comes back to pinned host memory;
+        # frames in flight as for `value`, each image read back on a copy stream
+        himgs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(F)]
+        copy_stream = torch.cuda.Stream(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        s3, e3 = E(), E()
+        s3.record(stream)
+        for s_ in streams:
+            s_.wait_event(s3)
+        done = [None] * F
+        for k in range(args.steps):
+            i = k % F
+            if done[i] is not None:
+                streams[i].wait_event(done[i])  # this slot's previous image has been read back
+            with torch.cuda.stream(streams[i]):
+                rs[i].frame(st, cams[pose_of(k)])
+                ev_ = torch.cuda.Event()
+                ev_.record(streams[i])
+            copy_stream.wait_event(ev_)
+            with torch.cuda.stream(copy_stream):
+                himgs[i].copy_(rs[i].image, non_blocking=True)
+                done[i] = torch.cuda.Event()
+                done[i].record(copy_stream)
+        stream.wait_stream(copy_stream)
+        e3.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        tr = max_over_ranks(s3.elapsed_time(e3), world, dev)
+        e2e_resident = dict(value=whole_job_rate(args.steps, world, tr), unit="frames/s", h2d_bytes_per_step=0,
+                            d2h_bytes_per_step=d2h,
+                            note="scene resident on the device, camera in as kernel parameters, image out")
 
     # the render with the optional inverse-depth output (outside the timed frames)
     inv = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -475,6 +508,7 @@ def main():
                         serial_frames_per_s=serial_fps,
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
             roofline=roofline, frame_roofline=frame_roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
+            e2e_resident_scene=e2e_resident,
             serving=serving, multiview=multiview,
             backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,

@@ -4,10 +4,11 @@ Requests (scene, camera) arrive over time.  Each is admitted when a slot
 and enough device memory (by a per-(scene, resolution) estimate) are free;
 its preprocess and sort then run at once on a stream of their own, so they
 overlap whatever batch is rendering.  Whenever the render engine is idle,
-every admitted request whose sort has finished joins one batch, rendered by
-a single persistent launch (gs_render_batch) replayed from a captured CUDA
-graph.  A request is complete when its batch's render has finished; its
-latency is completion time minus arrival time.
+every admitted request joins one batch, rendered by a single persistent
+launch (gs_render_batch) replayed from a captured CUDA graph; the launch
+waits for those requests' sorts on the device, not on the host.  A request
+is complete when its batch's render has finished; its latency is completion
+time minus arrival time.
 
 Every kernel runs in libgs.so; this module only schedules, allocates (from
 PyTorch's caching allocator) and keeps time.
@@ -215,11 +216,11 @@ class Server:
                     done.append(req)
                 self.stats["batches"] += 1
                 rendering = None
-            # launch a batch of every prepared request whose sort is done
+            # launch a batch of the prepared requests as soon as the render
+            # engine is free: the render stream waits for their sorts on the
+            # device, so no host round trip sits between a sort and its render
             if rendering is None and prepared:
-                ready = [p for p in prepared if p[2].query()]
-                if not ready and not pending and not realtime:
-                    ready = prepared[:1]
+                ready = prepared
                 if ready:
                     batch = ready[: self.max_batch]
                     for b in batch:

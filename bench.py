@@ -158,6 +158,36 @@ def oracle_frame_sample(scene, cam, rows_tiles: int, threads: int = 0):
                 sec_per_frame=sec_frame, cores=cores, m=srt["m"])
 
 
+_CONFIG1_CODE = r'''
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import oracle as O
+from synth import CONFIGS
+wl = CONFIGS["fwd_16k_256"]
+scene, cam = wl["scene"](), wl["cameras"]()[0]
+O.build_oracle()
+O.frame(scene, cam)  # warm-up
+t = time.perf_counter()
+pre, srt, img = O.frame(scene, cam, threads={threads})
+dt = time.perf_counter() - t
+print(json.dumps(dict(sec_per_frame=dt, evals=int(img["n_eval"].sum()))))
+'''
+
+
+def oracle_config1(threads: int) -> dict:
+    """The oracle on the whole 16k-Gaussian 256x256 frame, in a child
+    process with OMP_NUM_THREADS = threads (0: all cores)."""
+    env = dict(os.environ)
+    if threads > 0:
+        env["OMP_NUM_THREADS"] = str(threads)
+    out = subprocess.run([sys.executable, "-c", _CONFIG1_CODE.format(root=ROOT, threads=threads)], env=env,
+                         capture_output=True, text=True, timeout=600)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    r["evals_per_s"] = r["evals"] / r["sec_per_frame"]
+    r["threads"] = threads if threads > 0 else os.cpu_count()
+    return r
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -449,7 +479,7 @@ def main():
         preprocess=dict(ms=pre_ms, bytes=pre_bytes, gbs=pre_gbs, frac_hbm=pre_gbs / peaks["hbm_gbs"]),
         sort=dict(ms=sort_ms, instances=ms_mean),
         render_invdepth=dict(ms=inv_ms, note="render with the optional inverse-depth output, same poses"),
-        render=dict(ms=rend_ms, evals=evals_mean, tflops=render_tflops,
+        render=dict(ms=rend_ms, evals=evals_mean, evals_per_s=evals_mean / (rend_ms / 1000.0), tflops=render_tflops,
                     tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
     )
     # kernels per frame: preprocess; compact, 4 depth radix passes, offsets,
@@ -496,6 +526,10 @@ def main():
                    sample=f"one frame (pose {used[0]}): FP64 oracle preprocess ({s['pre_s']:.2f} s) and "
                           f"duplicate/sort ({s['sort_s']:.2f} s) in full, render of pixel rows {s['band_rows']} "
                           f"({s['render_band_s']:.2f} s) extrapolated to the whole image")
+        try:
+            cpu["config_fwd_16k_256"] = dict(one_thread=oracle_config1(1), all_cores=oracle_config1(0))
+        except (subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+            cpu["config_fwd_16k_256"] = dict(error=str(e)[:200])
 
     if rank == 0:
         line = dict(

@@ -40,13 +40,13 @@ template <bool kDepth>
 __device__ __forceinline__ void blend(Pixel &p, bool keep, float alpha, float r, float g, float b, float iz,
                                       uint32_t idx) {
     if (p.done || !keep) return;
-    const float Tn = p.T * (1.0f - alpha);
+    const float w = alpha * p.T;  // this splat's weight
+    const float Tn = p.T - w;     // T (1 - alpha)
     if (Tn < kTStop) {  // stop without blending this splat
         p.done = true;
         p.stop = idx;
         return;
     }
-    const float w = alpha * p.T;
     p.c0 = fmaf(r, w, p.c0);
     p.c1 = fmaf(g, w, p.c1);
     p.c2 = fmaf(b, w, p.c2);

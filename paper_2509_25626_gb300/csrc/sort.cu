@@ -653,22 +653,37 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 }
 
 // --- step 6: ranges ----------------------------------------------------------
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const SortHeader *__restrict__ hdr,
-                              uint32_t num_tiles, uint2 *__restrict__ ranges) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per tile: each lower-bound search probes 32 keys at once and
+// keeps the part of the range between the last probe below the target and
+// the first at or above it, so a search over M keys takes ~log33(M) + 1
+// dependent round trips (5 at M = 9.4e6) instead of log2(M).
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint64_t *__restrict__ keys, uint32_t n, uint64_t v,
+                                                     unsigned lane) {
+    uint32_t lo = 0, hi = n;  // keys[< lo] < v <= keys[>= hi]
+    while (hi - lo > 32u) {
+        const uint32_t len = hi - lo;
+        const uint32_t p = lo + (uint32_t)(((uint64_t)(lane + 1u) * len) / 33u);  // strictly increasing in lane
+        const unsigned below = __ballot_sync(0xffffffffu, keys[p] < v);
+        const uint32_t c = (uint32_t)__popc(below);  // probes 0 .. c-1 are below v
+        const uint32_t plo = __shfl_sync(0xffffffffu, p, c > 0u ? c - 1u : 0u);
+        const uint32_t phi = __shfl_sync(0xffffffffu, p, c < 32u ? c : 31u);
+        if (c > 0u) lo = plo + 1u;
+        if (c < 32u) hi = phi;
+    }
+    const bool below = lo + lane < hi && keys[lo + lane] < v;
+    return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, below));
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict__ keys,
+                                                     const SortHeader *__restrict__ hdr, uint32_t num_tiles,
+                                                     uint2 *__restrict__ ranges) {
+    const uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
     if (t >= num_tiles) return;
+    const unsigned lane = lane_id();
     const uint32_t n = hdr->m_sort;
-    auto lower = [&](uint64_t v) {
-        uint32_t lo = 0, hi = n;
-        while (lo < hi) {
-            const uint32_t mid = lo + (hi - lo) / 2;
-            if (keys[mid] < v) lo = mid + 1; else hi = mid;
-        }
-        return lo;
-    };
-    const uint32_t s = lower((uint64_t)t << 32);
-    const uint32_t e = lower((uint64_t)(t + 1) << 32);
-    ranges[t] = s < e ? make_uint2(s, e) : make_uint2(0u, 0u);
+    const uint32_t s = warp_lower_bound(keys, n, (uint64_t)t << 32, lane);
+    const uint32_t e = warp_lower_bound(keys, n, (uint64_t)(t + 1) << 32, lane);
+    if (lane == 0) ranges[t] = s < e ? make_uint2(s, e) : make_uint2(0u, 0u);
 }
 
 }  // namespace
@@ -723,7 +738,8 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
                     true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }
     }
-    ranges_kernel<<<(num_tiles + 255) / 256, 256, 0, st>>>(keys, ws.hdr, num_tiles, reinterpret_cast<uint2 *>(ranges));
+    ranges_kernel<<<(unsigned)(((uint64_t)num_tiles * 32 + 255) / 256), 256, 0, st>>>(
+        keys, ws.hdr, num_tiles, reinterpret_cast<uint2 *>(ranges));
     return cudaGetLastError();
 }
 

@@ -217,6 +217,14 @@ int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint3
                        const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, uint32_t *n_eval,
                        uint32_t *tile_cycles, void *stream);
 
+/* One forward frame: gs_preprocess, gs_sort (m_out = NULL: no host
+ * synchronisation; an overflow of m_cap is recorded in the workspace and
+ * read with gs_sort_status) and gs_render, enqueued on `stream` in one call.
+ * Arguments and errors as those calls. */
+int gs_frame(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, uint64_t *keys, uint32_t *vals,
+             int64_t m_cap, uint32_t *ranges, void *workspace, size_t workspace_bytes, const float bg[3],
+             float *out_color, float *final_T, uint32_t *n_contrib, void *stream);
+
 /* gs_render with optional outputs, each NULL to skip (the same per-pixel
  * blend, so out_color, final_T and n_contrib equal gs_render's bit for bit):
  *   invdepth [H][W] float: the inverse depth blended like a colour channel,

@@ -83,6 +83,9 @@ def lib():
         L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P, P]
         L.gs_render_ex.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float)] + [P] * 7
         L.gs_splat_buffer_bytes.argtypes = [ctypes.c_int64]
+        L.gs_frame.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P, P, ctypes.c_int64, P, P,
+                               c_size_t, ctypes.POINTER(c_float), P, P, P, P]
+        L.gs_frame.restype = ctypes.c_int
         L.gs_splat_buffer_bytes.restype = c_size_t
         L.gs_backward_workspace_bytes.argtypes = [c_int64]
         L.gs_backward_workspace_bytes.restype = c_size_t
@@ -112,7 +115,7 @@ def check(code: int, what: str) -> int:
 
 def exported_symbols():
     """Names of the gs_* functions the header declares."""
-    return ["gs_splat_buffer_bytes", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
+    return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
             "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
             "gs_render_backward",
             "gs_render_batch",

@@ -27,8 +27,7 @@ def camera_struct(cam) -> L.GsCamera:
     tan_fovx, tan_fovy attributes."""
     c = L.GsCamera()
     vm = np.ascontiguousarray(np.asarray(cam.viewmat, np.float32).reshape(16))
-    for i in range(16):
-        c.viewmat[i] = float(vm[i])
+    ctypes.memmove(c.viewmat, vm.ctypes.data, 64)
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
     c.tan_fovx, c.tan_fovy = float(cam.tan_fovx), float(cam.tan_fovy)
@@ -257,14 +256,25 @@ class Renderer:
         self.image = torch.empty((3, self.height, self.width), dtype=torch.float32, device=dev)
         self.final_T = torch.empty((self.height, self.width), dtype=torch.float32, device=dev)
         self.n_contrib = torch.empty((self.height, self.width), dtype=torch.int32, device=dev)
+        self._ptrs = [_ptr(t) for t in (self.splats, self.keys, self.vals, self.ranges, self.workspace, self.image,
+                                        self.final_T, self.n_contrib)]
+        self._ws_bytes = self.workspace.numel()
+        self._scene_key, self._scene_struct = None, None
 
     def frame(self, scene: SceneTensors, cam, bg=(0.0, 0.0, 0.0), stream=None):
+        """gs_frame: preprocess, sort and render in one call, no host sync."""
         if scene.n != self.n or int(cam.width) != self.width or int(cam.height) != self.height:
             raise ValueError("scene size or resolution differs from the Renderer's buffers")
-        preprocess(scene, cam, self.splats, stream)
-        sort(self.splats, self.n, cam, self.m_cap, self.keys, self.vals, self.ranges, self.workspace, count=False,
-             stream=stream)
-        render(self.splats, self.vals, self.ranges, cam, bg, self.image, self.final_T, self.n_contrib, stream)
+        key = (id(scene), scene.sh_degree) + tuple(int(t.data_ptr()) for t in
+                                                   (scene.means, scene.log_scales, scene.quats,
+                                                    scene.opacity_logits, scene.sh))
+        if self._scene_key != key:  # validate and build the scene struct once per scene
+            self._scene_struct, self._scene_key = scene.struct(), key
+        c = camera_struct(cam)
+        bgc = (ctypes.c_float * 3)(float(bg[0]), float(bg[1]), float(bg[2]))
+        p = self._ptrs
+        L.check(L.lib().gs_frame(ctypes.byref(self._scene_struct), ctypes.byref(c), p[0], p[1], p[2], self.m_cap,
+                                 p[3], p[4], self._ws_bytes, bgc, p[5], p[6], p[7], _stream(stream)), "gs_frame")
         return self.image, self.final_T, self.n_contrib
 
     def instances(self, stream=None):

@@ -185,6 +185,18 @@ int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t
     return cuda_status(launch_render_batch(desc, counter, grid, (cudaStream_t)stream));
 }
 
+int gs_frame(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, uint64_t *keys, uint32_t *vals,
+             int64_t m_cap, uint32_t *ranges, void *workspace, size_t workspace_bytes, const float bg[3],
+             float *out_color, float *final_T, uint32_t *n_contrib, void *stream) {
+    gs::NvtxRange nvtx_range("gs_frame");
+    if (!scene) return GS_ERR_INVALID_ARG;
+    int code = gs_preprocess(scene, cam, splats, stream);
+    if (code != GS_OK) return code;
+    code = gs_sort(splats, scene->n, cam, keys, vals, m_cap, ranges, workspace, workspace_bytes, nullptr, stream);
+    if (code != GS_OK) return code;
+    return gs_render(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, stream);
+}
+
 size_t gs_splat_buffer_bytes(int64_t n) { return (size_t)(n > 0 ? n : 0) * (sizeof(gs_splat) + sizeof(gs_sort_input)); }
 
 size_t gs_backward_workspace_bytes(int64_t n) { return (size_t)(n > 0 ? n : 1) * 12 * sizeof(float); }

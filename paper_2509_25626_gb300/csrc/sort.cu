@@ -42,9 +42,10 @@ constexpr int kThreads = 256;
 constexpr int kIpt = kSortTileItems / kThreads;  // 16 items per thread
 // Threads per block of the radix passes over arrays (4096 elements each).
 constexpr int kSweepThreads = 256;  // 512 measured slower
-// Predecessors read per round trip of the depth passes' look-back (wider
-// windows measured slower).
+// Predecessors read per round trip of the look-back walks (depth passes,
+// tile passes).
 constexpr int kDepthWin = 8;
+constexpr int kTileWin = 8;
 constexpr int kBins = 256;
 
 constexpr uint64_t kFlagAgg = 1ull << 62;        // block aggregate published
@@ -89,19 +90,22 @@ __device__ uint64_t wait_flag(const uint64_t *p, SortHeader *hdr) {
     }
 }
 
-// Decoupled look-back over `stride`-spaced words: publishes this block's
-// aggregate, sums predecessors back to the first inclusive prefix,
-// publishes this block's inclusive prefix; returns the exclusive prefix.
-// Predecessors are read kWin at a time (independent loads), so a walk over
-// many blocks that have only published aggregates costs few round trips.
+// Decoupled look-back over `stride`-spaced words, in two steps so that a
+// block can publish its aggregate as soon as it is known and walk later.
+// publish_aggregate: block 0 publishes its inclusive prefix at once.
+__device__ __forceinline__ void publish_aggregate(uint64_t *state, uint32_t block, uint32_t stride, uint64_t local) {
+    st_relaxed(state + (size_t)block * stride, (block == 0 ? kFlagPre : kFlagAgg) | local);
+}
+
+// walk_back: sums predecessors back to the first inclusive prefix,
+// publishes this block's inclusive prefix and returns the exclusive one.
+// Predecessors are read kWin at a time (independent loads): while the
+// blocks running together have only published aggregates, the inclusive
+// prefixes advance by about kWin blocks per round trip, so the window sets
+// the pass's block throughput.
 template <int kWin>
-__device__ uint64_t look_back(uint64_t *state, uint32_t block, uint32_t stride, uint64_t local, SortHeader *hdr) {
-    uint64_t *mine = state + (size_t)block * stride;
-    if (block == 0) {
-        st_relaxed(mine, kFlagPre | local);
-        return 0;
-    }
-    st_relaxed(mine, kFlagAgg | local);
+__device__ uint64_t walk_back(uint64_t *state, uint32_t block, uint32_t stride, uint64_t local, SortHeader *hdr) {
+    if (block == 0) return 0;
     uint64_t excl = 0;
     int64_t p = (int64_t)block - 1;
     bool found = false;
@@ -121,15 +125,31 @@ __device__ uint64_t look_back(uint64_t *state, uint32_t block, uint32_t stride, 
         p -= kWin;
         if (p < 0) found = true;  // block 0 always holds a prefix; defensive end of the walk
     }
-    st_relaxed(mine, kFlagPre | (excl + local));
+    st_relaxed(state + (size_t)block * stride, kFlagPre | (excl + local));
     return excl;
+}
+
+// The lanes of the warp whose valid 8-bit digit equals this lane's: one
+// ballot per bit (VOTE runs on the ALU pipes; MATCH goes through the
+// shared-memory pipe that the ranking already keeps busy).  Meaningful for
+// valid lanes only.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
+    unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned v = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
 }
 
 // Adds `count` to bin `d` of a shared histogram once per distinct value in
 // the warp (every lane must call; d = ~0u means "nothing to add").
 __device__ __forceinline__ void warp_hist_add(uint32_t *hist, uint32_t d) {
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (d != 0xffffffffu && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    const bool valid = d != 0xffffffffu;
+    const unsigned peers = digit_peers(d, valid);
+    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
 }
 
 // Exclusive prefix of `blk` for a scan: publish this block's aggregate, then
@@ -329,7 +349,6 @@ struct SweepSmemT {
     uint32_t vals[ITEMS];
     uint32_t wcnt[NT / 32][kBins];
     uint32_t base[kBins];
-    uint32_t dstart[kBins];
     uint32_t scratch[33];
 };
 using SweepSmem = SweepSmemT<kThreads>;
@@ -352,7 +371,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
     for (int k = 0; k < IPT; ++k) {
         const bool valid = wbase + k * 32 < n;
         const uint32_t d = valid ? ((key[k] >> shift) & 0xffu) : kBins;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = digit_peers(d, valid);
         uint32_t old = 0;
         if (valid) old = sm.wcnt[warp][d];
         __syncwarp();
@@ -371,28 +390,32 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
             cnt += c;
         }
     }
+    if (digit_thread) publish_aggregate(state + t, blk, kBins, cnt);
     uint32_t tot;
     const uint32_t dst = block_exclusive_scan(cnt, sm.scratch, &tot);
     const uint32_t dbase = block_exclusive_scan(digit_thread ? digit_total : 0u, sm.scratch, &tot);
-    if (digit_thread) {
-        sm.dstart[t] = dst;
-        const uint64_t excl = look_back<WIN>(state + t, blk, kBins, cnt, hdr);
-        sm.base[t] = dbase + (uint32_t)excl;
+    if (digit_thread) {  // fold the digit's start in the block into each warp's prefix
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) sm.wcnt[w][t] += dst;
     }
-    __syncthreads();
     uint32_t vals[IPT];
 #pragma unroll
     for (int k = 0; k < IPT; ++k) vals[k] = val(k);
-    __syncthreads();  // val() may read shared memory that the scatter below overwrites
+    __syncthreads();  // the warp prefixes are complete; val() may read shared memory that the scatter below overwrites
+    // block-local scatter before the walk: keys, ranks and values leave the
+    // registers, which the walk's window then uses
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
         if (wbase + k * 32 < n) {
             const uint32_t d = (key[k] >> shift) & 0xffu;
-            const uint32_t pos = sm.dstart[d] + sm.wcnt[warp][d] + rank[k];
+            const uint32_t pos = sm.wcnt[warp][d] + rank[k];
             sm.keys[pos] = key[k];
             sm.vals[pos] = vals[k];
         }
     }
+    // base[d]: global position of the block's first digit-d element, less its
+    // position in the block (mod 2^32), so that element j goes to base[d] + j
+    if (digit_thread) sm.base[t] = dbase + (uint32_t)walk_back<WIN>(state + t, blk, kBins, cnt, hdr) - dst;
     __syncthreads();
     const uint32_t cnt_blk = min((uint32_t)ITEMS, n - start);
     constexpr int kHalf = IPT / 2;
@@ -408,7 +431,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
                 kk[k] = sm.keys[j];
                 vv[k] = sm.vals[j];
                 const uint32_t d = (kk[k] >> shift) & 0xffu;
-                gp[k] = sm.base[d] + (j - sm.dstart[d]);
+                gp[k] = sm.base[d] + j;
             }
         }
         if (kFinal) {
@@ -648,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
     __syncthreads();
-    rank_scatter<kFinal, kThreads, 8, kSortTileItems>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+    rank_scatter<kFinal, kThreads, kTileWin, kSortTileItems>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
                          ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
 }
 
@@ -698,7 +721,7 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
     const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
     for (int p = 0; p < 4; ++p)
-        onesweep_kernel<false, kSweepThreads, kDepthWin, kSortTileItems><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+        onesweep_kernel<false, kSweepThreads, kDepthWin, kDepthItems><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
                                                          ws.hist_depth + kBins * p, false, ws.depth_state[p],
                                                          &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
@@ -728,12 +751,12 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
         for (int p = 1; p < passes; ++p) {
             const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
             if (p == passes - 1)
-                onesweep_kernel<true, kSweepThreads, 8, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
+                onesweep_kernel<true, kSweepThreads, kTileWin, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
                                                                 &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
                                                                 &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
                                                                 tx);
             else
-                onesweep_kernel<false, kSweepThreads, 8, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(
+                onesweep_kernel<false, kSweepThreads, kTileWin, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(
                     buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
                     true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
         }

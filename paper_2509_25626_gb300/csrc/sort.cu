@@ -413,11 +413,22 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
             sm.vals[pos] = vals[k];
         }
     }
+    const uint32_t cnt_blk = min((uint32_t)ITEMS, n - start);
+    // kFinal: the depth bits of each element's value, gathered in block order
+    // before the walk so that the gathers' latency overlaps it
+    uint32_t dv[kFinal ? IPT : 1];
+    if (kFinal) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const uint32_t j = t + k * NT;
+            dv[k] = j < cnt_blk ? depthv[sm.vals[j]] : 0u;
+        }
+    }
     // base[d]: global position of the block's first digit-d element, less its
     // position in the block (mod 2^32), so that element j goes to base[d] + j
     if (digit_thread) sm.base[t] = dbase + (uint32_t)walk_back<WIN>(state + t, blk, kBins, cnt, hdr) - dst;
     __syncthreads();
-    const uint32_t cnt_blk = min((uint32_t)ITEMS, n - start);
     constexpr int kHalf = IPT / 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -435,14 +446,11 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
             }
         }
         if (kFinal) {
-            uint32_t dv[kHalf];
-#pragma unroll
-            for (int k = 0; k < kHalf; ++k) dv[k] = gp[k] < n ? depthv[vv[k]] : 0u;  // batched gathers
 #pragma unroll
             for (int k = 0; k < kHalf; ++k)
                 if (gp[k] < n) {  // false only for idle slots (or inconsistent digit totals)
                     const uint32_t tile = (kk[k] >> shift_y) * tiles_x + (kk[k] & ((1u << shift_y) - 1u));
-                    kout64[gp[k]] = ((uint64_t)tile << 32) | dv[k];
+                    kout64[gp[k]] = ((uint64_t)tile << 32) | dv[kFinal ? h * kHalf + k : 0];
                     vout[gp[k]] = vv[k];
                 }
         } else {

@@ -492,8 +492,11 @@ def main():
         roofline["frac_at_sampled_clock"] = render_tflops / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
     kernels = dict(
         preprocess=dict(ms=pre_ms, bytes=pre_bytes, gbs=pre_gbs, frac_hbm=pre_gbs / peaks["hbm_gbs"]),
-        sort=dict(ms=sort_ms, instances=ms_mean),
-        render_invdepth=dict(ms=inv_ms, note="render with the optional inverse-depth output, same poses"),
+        sort=dict(ms=sort_ms, instances=ms_mean),  # bytes and fraction below, with the frame roofline
+        render_invdepth=dict(ms=inv_ms, tflops=evals_mean * FLOP_PER_EVAL / (inv_ms / 1000.0) / 1e12,
+                             frac=evals_mean * FLOP_PER_EVAL / (inv_ms / 1000.0) / 1e12 / fp32_peak,
+                             note="render with the optional inverse-depth output, same poses; work as the "
+                                  "render's (the depth channel's FMA not counted)"),
         render=dict(ms=rend_ms, evals=evals_mean, evals_per_s=evals_mean / (rend_ms / 1000.0), tflops=render_tflops,
                     tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
     )
@@ -518,6 +521,9 @@ def main():
     floors = dict(preprocess_ms=pre_bytes / (peaks["hbm_gbs"] * 1e6),
                   sort_ms=sort_bytes / (peaks["hbm_gbs"] * 1e6),
                   render_ms=evals_mean * FLOP_PER_EVAL / (fp32_peak * 1e9))
+    kernels["sort"].update(bytes=sort_bytes, gbs=sort_bytes / (sort_ms / 1000.0) / 1e9,
+                           frac_hbm=sort_bytes / (sort_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                           bound="latency and issue; fraction of its algorithmic bytes at HBM speed")
     frame_roofline = dict(floor_ms=sum(floors.values()), frame_ms=1000.0 / serial_fps,
                           frac=sum(floors.values()) / (1000.0 / serial_fps), **floors,
                           sort_bytes=sort_bytes)
@@ -723,8 +729,55 @@ def measure_backward(gs, dev, steps: int, warmup: int):
     e.record()
     torch.cuda.synchronize(dev)
     ms = s.elapsed_time(e) / steps
+
+    # the backward's two kernels timed apart on the forward's outputs, with
+    # their roofline fractions: the backward render against the FP32 issue
+    # peak (work: the evaluations it walks, sum of n_contrib over pixels,
+    # x the forward's 25 FLOP of recomputation -- a lower bound, the gradient
+    # terms of blended evaluations come on top); the preprocess backward
+    # against HBM (bytes it must move: the tiles word and the 236 B of
+    # gradients of every Gaussian, plus the 2D gradients (48 B) and the
+    # parameters (236 B) of the visible ones)
+    st = gs.SceneTensors.from_scene(scene, dev)
+    n = scene.n
+    dsplat = torch.empty((n, 12), dtype=torch.float32, device=dev)
+    grads = {k: torch.empty_like(getattr(st, k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    t_rb = t_pb = 0.0
+    evals = vis = 0
+    reps = len(cams)
+    for k in range(reps + 1):  # the first pass warms up
+        cam = cams[k % len(cams)]
+        sp = gs.preprocess(st, cam)
+        _, vals, ranges, _, _ = gs.sort(sp, n, cam, 8 * n)
+        _, T, nc = gs.render(sp, vals, ranges, cam)
+        a, b, c = E(), E(), E()
+        a.record()
+        gs.render_backward_splats(cam, sp, n, vals, ranges, T, nc, dL, dsplat=dsplat)
+        b.record()
+        gs.preprocess_backward(st, cam, sp, dsplat, grads)
+        c.record()
+        torch.cuda.synchronize(dev)
+        if k > 0:
+            t_rb += a.elapsed_time(b) / reps
+            t_pb += b.elapsed_time(c) / reps
+            evals += int(nc.to(torch.int64).sum().item())
+            vis += int((sp[:n].view(torch.int32)[:, 13] > 0).sum().item())
+    evals /= reps
+    vis /= reps
+    rb_tflops = evals * FLOP_PER_EVAL / (t_rb / 1000.0) / 1e12
+    pb_bytes = n * (4 + 236) + vis * (48 + 236)
+    pb_gbs = pb_bytes / (t_pb / 1000.0) / 1e9
+    kernels = dict(
+        render_backward=dict(ms=t_rb, evals=evals, tflops=rb_tflops, frac=rb_tflops / fp32_peak, bound="alu",
+                             work=f"{evals:.4g} evaluations (sum of n_contrib) x {FLOP_PER_EVAL} FLOP, lower bound"),
+        preprocess_backward=dict(ms=t_pb, bytes=pb_bytes, gbs=pb_gbs, frac_hbm=pb_gbs / peaks["hbm_gbs"],
+                                 bound="hbm"))
     return dict(workload="bwd_1m_1237x822", gaussians=scene.n, width=cams[0].width, height=cams[0].height,
-                steps=steps, ms_per_step=ms, steps_per_s=1000.0 / ms,
+                steps=steps, ms_per_step=ms, steps_per_s=1000.0 / ms, kernels=kernels,
                 note="forward + backward through gs.rasterize (one host sync per forward for the sort's M)")
 
 

@@ -197,11 +197,33 @@ size_t gs_backward_workspace_bytes(int64_t n);
  * clamp and clamped colour channels pass no gradient; the tile lists and the
  * sort are constant.  splats, vals, ranges, final_T, n_contrib: the forward's
  * outputs.  workspace: gs_backward_workspace_bytes(n) bytes, 16-byte aligned.
- * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+ * Equivalent to gs_render_backward_splats into the workspace, then
+ * gs_preprocess_backward.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_render_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const uint32_t *vals,
                        const uint32_t *ranges, const float bg[3], const float *final_T, const uint32_t *n_contrib,
                        const float *dL_dcolor, void *workspace, size_t workspace_bytes,
                        const gs_scene_grads *grads, void *stream);
+
+/* The first half of gs_render_backward: the per-splat 2D gradients alone
+ * (Eq. 1 differentiated per pixel, as above).  dsplat: float [n][12]
+ * (device, 16-byte aligned), zeroed by the call and filled with
+ * dL/d(x, y, conic a, b, c, opacity, r, g, b) per Gaussian (3 floats
+ * unused); Gaussians in no list get zeros.  The pixel-space mean gradient is
+ * what densification heuristics read.  Other arguments as for
+ * gs_render_backward, n = the scene's Gaussian count.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_render_backward_splats(const gs_camera *cam, const gs_splat *splats, int64_t n, const uint32_t *vals,
+                              const uint32_t *ranges, const float bg[3], const float *final_T,
+                              const uint32_t *n_contrib, const float *dL_dcolor, float *dsplat, void *stream);
+
+/* The second half of gs_render_backward: the chain rule from the per-splat
+ * gradients dsplat (gs_render_backward_splats' output, float [n][12],
+ * device) through the preprocessing of Section II-B (1) to the scene
+ * parameters.  splats: gs_preprocess's output for the same scene and camera.
+ * Every gradient array is written in full (zeros for culled Gaussians).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_preprocess_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const float *dsplat,
+                           const gs_scene_grads *grads, void *stream);
 
 /* gs_render plus, per pixel, the number of splats evaluated before the
  * pixel stopped (the stopping splat included; all of the tile's splats if it

@@ -10,6 +10,8 @@ from .api import (  # noqa: F401
     RasterizeGaussians,
     rasterize,
     render_backward,
+    render_backward_splats,
+    preprocess_backward,
     SceneTensors,
     camera_struct,
     num_tiles,

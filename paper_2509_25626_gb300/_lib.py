@@ -93,6 +93,12 @@ def lib():
                                          ctypes.POINTER(c_float), P, P, P, P, c_size_t,
                                          ctypes.POINTER(GsSceneGrads), P]
         L.gs_render_backward.restype = ctypes.c_int
+        L.gs_render_backward_splats.argtypes = [ctypes.POINTER(GsCamera), P, c_int64, P, P, ctypes.POINTER(c_float),
+                                                P, P, P, P, P]
+        L.gs_render_backward_splats.restype = ctypes.c_int
+        L.gs_preprocess_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P,
+                                             ctypes.POINTER(GsSceneGrads), P]
+        L.gs_preprocess_backward.restype = ctypes.c_int
         L.gs_strerror.argtypes = [ctypes.c_int]
         L.gs_strerror.restype = ctypes.c_char_p
         L.gs_last_cuda_error.restype = ctypes.c_char_p
@@ -117,6 +123,6 @@ def exported_symbols():
     """Names of the gs_* functions the header declares."""
     return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
             "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
-            "gs_render_backward",
+            "gs_render_backward", "gs_render_backward_splats", "gs_preprocess_backward",
             "gs_render_batch",
             "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

@@ -380,6 +380,41 @@ def render_backward(scene: SceneTensors, cam, splats, vals, ranges, final_T, n_c
     return grads, workspace.view(-1, 12)[:max(n, 1)]
 
 
+def render_backward_splats(cam, splats, n, vals, ranges, final_T, n_contrib, dL_dcolor, bg=(0.0, 0.0, 0.0),
+                           dsplat=None, stream=None):
+    """gs_render_backward_splats: the per-splat 2D gradients [n, 12]
+    (dL/d x, y, conic a, b, c, opacity, r, g, b; 3 unused)."""
+    n = int(n)
+    if dsplat is None:
+        dsplat = torch.empty((max(n, 1), 12), dtype=torch.float32, device=splats.device)
+    _check_tensor(dsplat, torch.float32, "dsplat")
+    dL = dL_dcolor.contiguous().to(torch.float32)
+    _check_tensor(dL, torch.float32, "dL_dcolor")
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    L.check(L.lib().gs_render_backward_splats(ctypes.byref(c), _ptr(splats), n, _ptr(vals), _ptr(ranges), bgc,
+                                              _ptr(final_T), _ptr(n_contrib), _ptr(dL), _ptr(dsplat),
+                                              _stream(stream)), "gs_render_backward_splats")
+    return dsplat
+
+
+def preprocess_backward(scene: SceneTensors, cam, splats, dsplat, grads=None, stream=None):
+    """gs_preprocess_backward: the scene gradients (a dict like
+    render_backward's) from the per-splat 2D gradients."""
+    if grads is None:
+        grads = {k: torch.empty_like(getattr(scene, k)) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                                      "sh")}
+    _check_tensor(dsplat, torch.float32, "dsplat")
+    g = L.GsSceneGrads()
+    g.dmeans, g.dlog_scales, g.dquats = grads["means"].data_ptr(), grads["log_scales"].data_ptr(), \
+        grads["quats"].data_ptr()
+    g.dopacity_logits, g.dsh = grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr()
+    c = camera_struct(cam)
+    L.check(L.lib().gs_preprocess_backward(ctypes.byref(scene.struct()), ctypes.byref(c), _ptr(splats),
+                                           _ptr(dsplat), ctypes.byref(g), _stream(stream)), "gs_preprocess_backward")
+    return grads
+
+
 class RasterizeGaussians(torch.autograd.Function):
     """image = render(preprocess(scene), sort) with the CUDA backward.
 

@@ -32,6 +32,12 @@ cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, cons
                                    const uint32_t *vals, const uint32_t *ranges, const float bg[3],
                                    const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
                                    float *dsplat, const gs_scene_grads &g, cudaStream_t st);
+cudaError_t launch_render_backward_splats(int64_t n, const CamParams &cam, const gs_splat *splats,
+                                          const uint32_t *vals, const uint32_t *ranges, const float bg[3],
+                                          const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
+                                          float *dsplat, cudaStream_t st);
+cudaError_t launch_preprocess_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
+                                       const float *dsplat, const gs_scene_grads &g, cudaStream_t st);
 cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
@@ -200,6 +206,40 @@ int gs_frame(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, uint
 size_t gs_splat_buffer_bytes(int64_t n) { return (size_t)(n > 0 ? n : 0) * (sizeof(gs_splat) + sizeof(gs_sort_input)); }
 
 size_t gs_backward_workspace_bytes(int64_t n) { return (size_t)(n > 0 ? n : 1) * 12 * sizeof(float); }
+
+int gs_render_backward_splats(const gs_camera *cam, const gs_splat *splats, int64_t n, const uint32_t *vals,
+                              const uint32_t *ranges, const float bg[3], const float *final_T,
+                              const uint32_t *n_contrib, const float *dL_dcolor, float *dsplat, void *stream) {
+    gs::NvtxRange nvtx_range("gs_render_backward_splats");
+    if (!camera_ok(cam) || !bg || n < 0 || n > (int64_t)UINT32_MAX) return GS_ERR_INVALID_ARG;
+    if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
+    if (!ranges || !aligned(ranges, 8) || !final_T || !n_contrib || !dL_dcolor || !aligned(final_T, 4) ||
+        !aligned(n_contrib, 4) || !aligned(dL_dcolor, 4) || !dsplat || !aligned(dsplat, 16))
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!splats || !aligned(splats, 16) || !vals)) return GS_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_backward_splats(n, make_cam_params(*cam), splats, vals, ranges, bg, final_T,
+                                                     n_contrib, dL_dcolor, dsplat, (cudaStream_t)stream));
+}
+
+int gs_preprocess_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const float *dsplat,
+                           const gs_scene_grads *grads, void *stream) {
+    gs::NvtxRange nvtx_range("gs_preprocess_backward");
+    if (!scene || !camera_ok(cam) || !grads) return GS_ERR_INVALID_ARG;
+    if (scene->n < 0 || scene->n > (int64_t)UINT32_MAX || scene->sh_degree < 0 || scene->sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        const void *ptrs[] = {scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh,
+                              splats, dsplat, grads->dmeans, grads->dlog_scales, grads->dquats,
+                              grads->dopacity_logits, grads->dsh};
+        for (const void *p : ptrs)
+            if (!p || !aligned(p, 4)) return GS_ERR_INVALID_ARG;
+        if (!aligned(scene->quats, 16) || !aligned(splats, 16)) return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_preprocess_backward(*scene, make_cam_params(*cam), splats, dsplat, *grads,
+                                                  (cudaStream_t)stream));
+}
 
 int gs_render_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const uint32_t *vals,
                        const uint32_t *ranges, const float bg[3], const float *final_T, const uint32_t *n_contrib,

@@ -463,21 +463,38 @@ __device__ __forceinline__ void preprocess_backward_one(
 
 }  // namespace
 
-cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
-                                   const uint32_t *vals, const uint32_t *ranges, const float bg[3],
-                                   const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
-                                   float *dsplat, const gs_scene_grads &g, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(dsplat, 0, sizeof(float) * 12 * (size_t)(s.n > 0 ? s.n : 1), st);
+// Per-splat 2D gradients: dsplat [n][12] zeroed, then accumulated per tile.
+cudaError_t launch_render_backward_splats(int64_t n, const CamParams &cam, const gs_splat *splats,
+                                          const uint32_t *vals, const uint32_t *ranges, const float bg[3],
+                                          const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
+                                          float *dsplat, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(dsplat, 0, sizeof(float) * 12 * (size_t)(n > 0 ? n : 1), st);
     if (e != cudaSuccess) return e;
     const int num_tiles = cam.tiles_x * cam.tiles_y;
     render_backward_kernel<<<num_tiles, kThreads, 0, st>>>(splats, vals, reinterpret_cast<const uint2 *>(ranges),
                                                             cam.width, cam.height, cam.tiles_x, bg[0], bg[1], bg[2],
                                                             final_T, n_contrib, dL_dcolor, dsplat);
+    return cudaGetLastError();
+}
+
+// The chain rule from the per-splat gradients to the scene parameters.
+cudaError_t launch_preprocess_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
+                                       const float *dsplat, const gs_scene_grads &g, cudaStream_t st) {
     if (s.n > 0)
         preprocess_backward_kernel<<<(unsigned)((s.n + kPreBackThreads - 1) / kPreBackThreads), kPreBackThreads, 0, st>>>(
             s.means, s.log_scales, reinterpret_cast<const float4 *>(s.quats), s.opacity_logits, s.sh, s.n,
             s.sh_degree, cam, splats, dsplat, g.dmeans, g.dlog_scales, g.dquats, g.dopacity_logits, g.dsh);
     return cudaGetLastError();
+}
+
+cudaError_t launch_render_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
+                                   const uint32_t *vals, const uint32_t *ranges, const float bg[3],
+                                   const float *final_T, const uint32_t *n_contrib, const float *dL_dcolor,
+                                   float *dsplat, const gs_scene_grads &g, cudaStream_t st) {
+    cudaError_t e = launch_render_backward_splats(s.n, cam, splats, vals, ranges, bg, final_T, n_contrib, dL_dcolor,
+                                                  dsplat, st);
+    if (e != cudaSuccess) return e;
+    return launch_preprocess_backward(s, cam, splats, dsplat, g, st);
 }
 
 }  // namespace gs

@@ -132,3 +132,27 @@ def test_backward_culled_and_empty():
     empty = subset_scene(sc, np.arange(0))
     g0, img0, _ = gpu_grads(empty, cam, dL)
     assert np.allclose(img0[0], BG[0]) and all(v.size == 0 for v in g0.values())
+
+
+def test_split_backward_equals_combined():
+    """gs_render_backward_splats then gs_preprocess_backward give what
+    gs_render_backward gives: the per-splat gradients within the reordering
+    of float atomics, and the scene gradients from identical per-splat
+    gradients bit for bit."""
+    sc, cam = clustered_scene(20000, seed=6), orbit_camera(2, 20, 4.0, 160, 120)
+    st = SceneTensors.from_scene(sc, DEV)
+    sp = gs.preprocess(st, cam)
+    _, vals, ranges, _, _ = gs.sort(sp, sc.n, cam, 64 * sc.n)
+    _, T, nc = gs.render(sp, vals, ranges, cam, BG)
+    dL = torch.randn((3, cam.height, cam.width), generator=torch.Generator().manual_seed(5)).to(DEV)
+    grads, dsplat = gs.render_backward(st, cam, sp, vals, ranges, T, nc, dL, BG)
+    ds = gs.render_backward_splats(cam, sp, sc.n, vals, ranges, T, nc, dL, BG)
+    torch.cuda.synchronize()
+    a, b = ds.cpu().numpy().astype(np.float64), dsplat.cpu().numpy().astype(np.float64)
+    assert rel_err(a, b) <= 1e-5
+    # culled Gaussians (no list) get exact zeros
+    tiles = sp[: sc.n].view(torch.int32)[:, 13].cpu().numpy()
+    assert np.all(a[tiles == 0] == 0)
+    g2 = gs.preprocess_backward(st, cam, sp, dsplat.contiguous())
+    for k in NAMES:
+        assert torch.equal(g2[k], grads[k]), k

@@ -48,6 +48,10 @@ def parse_args():
     p.add_argument("--profile-frames", type=int, default=0,
                    help="profiler driver: one sizing sort, then this many frames of pose 0 one after another "
                         "(launch order: preprocess + 9 sort kernels, then 11 kernels per frame); no timing")
+    p.add_argument("--profile-backward", type=int, default=0,
+                   help="profiler driver: forward of the 1M-Gaussian 1237x822 backward workload (pose 0), then this "
+                        "many backward passes (per pass: gs_render_backward_splats, gs_preprocess_backward); no "
+                        "timing")
     return p.parse_args()
 
 
@@ -257,6 +261,23 @@ def main():
     import paper_2509_25626_gb300 as gs
     from paper_2509_25626_gb300 import _lib as L
     from synth import CONFIGS
+
+    if args.profile_backward > 0:  # fixed launch sequence for ncu captures
+        wb = CONFIGS["bwd_1m_1237x822"]
+        sb, cb = wb["scene"](), wb["cameras"]()[0]
+        stb = gs.SceneTensors.from_scene(sb, dev)
+        sp = gs.preprocess(stb, cb)
+        _, vals, ranges, _, _ = gs.sort(sp, sb.n, cb, 8 * sb.n)
+        _, Tb, ncb = gs.render(sp, vals, ranges, cb)
+        dLb = torch.randn((3, cb.height, cb.width), generator=torch.Generator().manual_seed(0)).to(dev)
+        dsplat = torch.empty((sb.n, 12), dtype=torch.float32, device=dev)
+        for _ in range(args.profile_backward):
+            gs.render_backward_splats(cb, sp, sb.n, vals, ranges, Tb, ncb, dLb, dsplat=dsplat)
+            gs.preprocess_backward(stb, cb, sp, dsplat)
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile_backward": args.profile_backward, "workload": "bwd_1m_1237x822"}))
+        return 0
 
     wl = CONFIGS[args.workload]
     scene = wl["scene"]()

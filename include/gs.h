@@ -219,8 +219,7 @@ int gs_render_backward_splats(const gs_camera *cam, const gs_splat *splats, int6
 /* The second half of gs_render_backward: the chain rule from the per-splat
  * gradients dsplat (gs_render_backward_splats' output, float [n][12],
  * device) through the preprocessing of Section II-B (1) to the scene
- * parameters.  splats: gs_preprocess's output for the same scene and camera
- * (the whole splat buffer: the records and the sort inputs after them).
+ * parameters.  splats: gs_preprocess's output for the same scene and camera.
  * Every gradient array is written in full (zeros for culled Gaussians).
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_preprocess_backward(const gs_scene *scene, const gs_camera *cam, const gs_splat *splats, const float *dsplat,

@@ -167,13 +167,7 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
                 s_c[k] = c.x;
                 s_o[k] = ex2_approx(-b.y);  // 1 / opacity
                 s_gid[k] = gid;
-                const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
-                const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
-                const uint32_t mx1 = (xhi >= tx0 + 8.f) & (xlo <= tx0 + 15.f);
-                const uint32_t my0 = (yhi >= ty0) & (ylo <= ty0 + 7.f);
-                const uint32_t my1 = (yhi >= ty0 + 8.f) & (ylo <= ty0 + 15.f);
-                m = (mx0 & my0) | ((mx1 & my0) << 1) | ((mx0 & my1) << 2) | ((mx1 & my1) << 3);
-                if (!(c.y >= 0.f)) m = 0;
+                m = quarter_mask(a, b, c, tx0, ty0);
             }
             s_mask[k] = (uint8_t)m;
         }

@@ -42,6 +42,40 @@ constexpr float kCullAbs = 1.0f / 64.0f;
 // log2(255): alpha >= 1/255  <=>  log2_opacity - (u^2 + v^2) >= -log2(255)
 constexpr float kLog2_255 = 7.994353436858858f;
 
+// Which 8x8 quarters of the 16x16 tile whose top-left pixel is (tx0, ty0) a
+// splat's alpha >= 1/255 region can reach, from the first three vectors of
+// its record: a = (x, y, w00, w01), b = (w11, ...), c = (..., hx, hy, ...).
+// Bit 2 qy + qx stands for the quarter of pixels [tx0 + 8 qx, +7] x
+// [ty0 + 8 qy, +7].  A quarter is ruled out by either of two separating
+// tests, each necessary for alpha >= 1/255 at one of its pixel centres:
+//  - the bounding box [x - hx, x + hx] x [y - hy, y + hy] misses it;
+//  - the band |u| <= R misses it, where u = w00 dx + w01 dy is the first
+//    component of W d (the render keeps a splat iff u^2 + v^2 <= R^2 =
+//    log2 o + log2 255, so |u| <= R).  u is affine in the pixel, so over a
+//    quarter it spans u(centre) +- 3.5 (|w00| + |w01|).
+// R is taken as hy w11 + 1/64 >= sqrt(log2 o + log2 255)(1 + 2^-10) + 1/64
+// (hy carries the box slack), a margin that covers the FP32 rounding of u
+// here and in the render (|w| <= ~1.6 after the 0.3 dilation and |d| within
+// a few thousand pixels put it near 1e-3).  The band removes the quarters
+// the box keeps only because the ellipse is thin and slanted.
+__device__ __forceinline__ uint32_t quarter_mask(const float4 a, const float4 b, const float4 c, float tx0,
+                                                 float ty0) {
+    if (!(c.y >= 0.f)) return 0u;  // alpha < 1/255 everywhere (empty box)
+    const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
+    const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
+    const uint32_t mx1 = (xhi >= tx0 + 8.f) & (xlo <= tx0 + 15.f);
+    const uint32_t my0 = (yhi >= ty0) & (ylo <= ty0 + 7.f);
+    const uint32_t my1 = (yhi >= ty0 + 8.f) & (ylo <= ty0 + 15.f);
+    const uint32_t box = (mx0 & my0) | ((mx1 & my0) << 1) | ((mx0 & my1) << 2) | ((mx1 & my1) << 3);
+    // u at the quarter centres (tx0 + 3.5 + 8 qx, ty0 + 3.5 + 8 qy)
+    const float u00 = fmaf(a.z, a.x - (tx0 + 3.5f), a.w * (a.y - (ty0 + 3.5f)));
+    const float u10 = fmaf(-8.f, a.z, u00), u01 = fmaf(-8.f, a.w, u00), u11 = fmaf(-8.f, a.w, u10);
+    const float L = fmaf(c.z, b.x, 1.0f / 64.0f) + 3.5f * (fabsf(a.z) + fabsf(a.w));
+    const uint32_t band = (uint32_t)(fabsf(u00) <= L) | ((uint32_t)(fabsf(u10) <= L) << 1) |
+                          ((uint32_t)(fabsf(u01) <= L) << 2) | ((uint32_t)(fabsf(u11) <= L) << 3);
+    return box & band;
+}
+
 // Camera as the kernels see it (kernel parameter, passed by value).
 struct CamParams {
     float V[12];          // rows 0..2 of the world->camera matrix

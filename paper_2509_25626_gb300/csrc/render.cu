@@ -5,11 +5,13 @@
 // and each lane two horizontally adjacent pixels, which share every term
 // that depends only on the row (dy, v, the w01 dy product).  Per round the
 // block stages up to 256 of the tile's splats in shared memory (two gathers
-// per thread) and marks, per warp, the splats whose alpha >= 1/255 bounding
-// box (gs_splat.cull_hx/hy) meets that warp's 8x8 block; each warp then
-// walks only its marked splats, front to back.  A splat left out has alpha
-// < 1/255 at every pixel of the block, so the per-pixel result, n_contrib
-// (a list position) and the stopping point are unchanged.
+// per thread) and marks, per warp, the splats whose alpha >= 1/255 region
+// can reach that warp's 8x8 block (quarter_mask: the bounding box
+// gs_splat.cull_hx/hy, and a slanted band along the first row of the
+// inverse-covariance factor); each warp then walks only its marked splats,
+// front to back.  A splat left out has alpha < 1/255 at every pixel of the
+// block, so the per-pixel result, n_contrib (a list position) and the
+// stopping point are unchanged.
 //
 // Exits are block-uniform (__syncthreads_and at the round boundary) and
 // warp-uniform inside a round, so no thread leaves while others still reach
@@ -121,14 +123,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
                 s_b[k] = StagedB{b.x, b.y, b.z, b.w};
                 s_c[k] = c.x;
                 if (kDepth) sm.iz[k] = __frcp_rn(__ldg(reinterpret_cast<const float *>(src + 3)));
-                // box [x - hx, x + hx] x [y - hy, y + hy] against the 8x8 blocks
-                const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
-                const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
-                const uint32_t mx1 = (xhi >= tx0 + 8.f) & (xlo <= tx0 + 15.f);
-                const uint32_t my0 = (yhi >= ty0) & (ylo <= ty0 + 7.f);
-                const uint32_t my1 = (yhi >= ty0 + 8.f) & (ylo <= ty0 + 15.f);
-                m = (mx0 & my0) | ((mx1 & my0) << 1) | ((mx0 & my1) << 2) | ((mx1 & my1) << 3);
-                if (!(c.y >= 0.f)) m = 0;  // alpha < 1/255 everywhere (empty box)
+                m = quarter_mask(a, b, c, tx0, ty0);
             }
             s_mask[k] = (uint8_t)m;
         }

@@ -17,6 +17,7 @@ from .scenes import (  # noqa: F401
     clustered_scene,
     slab_scene,
     tiny_scene,
+    needle_scene,
     concat_scenes,
     subset_scene,
 )

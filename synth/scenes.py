@@ -237,6 +237,24 @@ def tiny_scene(n: int, seed: int, width: int, height: int, fov_x_deg: float = 60
     return Scene(_f32(means), _f32(log_scales), quats, _f32(logits), _sh(rng, n)), cam
 
 
+def needle_scene(n: int, seed: int, width: int, height: int) -> tuple[Scene, Camera]:
+    """Needle-like Gaussians at every orientation in front of a camera at the
+    origin: one long axis (log-scale N(-1.8, 0.3)) and two thin ones
+    (N(-6, 0.3)), uniformly random rotations, so that their projected
+    ellipses are thin and slanted at every angle."""
+    rng = np.random.default_rng(seed)
+    cam = pinhole_camera(width, height, 60.0)
+    z = rng.uniform(1.5, 4.0, size=n)
+    x = rng.uniform(-1.1, 1.1, size=n) * cam.tan_fovx * z
+    y = rng.uniform(-1.1, 1.1, size=n) * cam.tan_fovy * z
+    means = np.stack([x, y, z], axis=1)
+    log_scales = np.stack([rng.normal(-1.8, 0.3, size=n), rng.normal(-6.0, 0.3, size=n),
+                           rng.normal(-6.0, 0.3, size=n)], axis=1)
+    quats = _unit_quats(rng, n)
+    logits = rng.normal(1.0, 1.0, size=n)
+    return Scene(_f32(means), _f32(log_scales), quats, _f32(logits), _sh(rng, n)), cam
+
+
 def concat_scenes(scenes) -> Scene:
     return Scene(*[_f32(np.concatenate(parts, axis=0)) for parts in zip(*[s.arrays() for s in scenes])])
 

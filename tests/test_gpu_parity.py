@@ -13,7 +13,7 @@ import paper_2509_25626_gb300 as gs
 from paper_2509_25626_gb300 import SPLAT_DTYPE, SceneTensors
 from parity import (ambiguous_gaussians, check_sorted_output, compare_images, compare_preprocess, flip_tile_mask,
                     rect_of, records_from_oracle, POS_EPS_E2E, TAU_ALPHA, TAU_T)
-from synth import clustered_scene, orbit_camera, pinhole_camera, tiny_scene, uniform_box_scene, Scene
+from synth import clustered_scene, needle_scene, orbit_camera, pinhole_camera, tiny_scene, uniform_box_scene, Scene
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +58,10 @@ def scenes_small():
     clu = clustered_scene(60000, seed=1)
     for k in (0, 7, 13):
         out.append((f"clustered60k_orbit{k}", clu, orbit_camera(k, 20, 4.0, 320, 240)))
+    # thin ellipses at every angle: the render's per-warp culling (box and
+    # slanted band) may leave out only splats below 1/255 on a whole quarter
+    sc, cam = needle_scene(3000, 21, 200, 150)
+    out.append(("needles3k_200x150", sc, cam))
     return out
 
 

@@ -61,14 +61,17 @@ constexpr float kLog2_255 = 7.994353436858858f;
 __device__ __forceinline__ uint32_t quarter_mask(const float4 a, const float4 b, const float4 c, float tx0,
                                                  float ty0) {
     if (!(c.y >= 0.f)) return 0u;  // alpha < 1/255 everywhere (empty box)
-    const float xlo = a.x - c.y, xhi = a.x + c.y, ylo = a.y - c.z, yhi = a.y + c.z;
-    const uint32_t mx0 = (xhi >= tx0) & (xlo <= tx0 + 7.f);
-    const uint32_t mx1 = (xhi >= tx0 + 8.f) & (xlo <= tx0 + 15.f);
-    const uint32_t my0 = (yhi >= ty0) & (ylo <= ty0 + 7.f);
-    const uint32_t my1 = (yhi >= ty0 + 8.f) & (ylo <= ty0 + 15.f);
+    // coordinates relative to the tile's first pixel (the slack in hx, hy
+    // and R covers the rounding of these differences)
+    const float x = a.x - tx0, y = a.y - ty0;
+    const float xlo = x - c.y, xhi = x + c.y, ylo = y - c.z, yhi = y + c.z;
+    const uint32_t mx0 = (xhi >= 0.f) & (xlo <= 7.f);
+    const uint32_t mx1 = (xhi >= 8.f) & (xlo <= 15.f);
+    const uint32_t my0 = (yhi >= 0.f) & (ylo <= 7.f);
+    const uint32_t my1 = (yhi >= 8.f) & (ylo <= 15.f);
     const uint32_t box = (mx0 & my0) | ((mx1 & my0) << 1) | ((mx0 & my1) << 2) | ((mx1 & my1) << 3);
-    // u at the quarter centres (tx0 + 3.5 + 8 qx, ty0 + 3.5 + 8 qy)
-    const float u00 = fmaf(a.z, a.x - (tx0 + 3.5f), a.w * (a.y - (ty0 + 3.5f)));
+    // u at the quarter centres (3.5 + 8 qx, 3.5 + 8 qy)
+    const float u00 = fmaf(a.z, x - 3.5f, a.w * (y - 3.5f));
     const float u10 = fmaf(-8.f, a.z, u00), u01 = fmaf(-8.f, a.w, u00), u11 = fmaf(-8.f, a.w, u10);
     const float L = fmaf(c.z, b.x, 1.0f / 64.0f) + 3.5f * (fabsf(a.z) + fabsf(a.w));
     const uint32_t band = (uint32_t)(fabsf(u00) <= L) | ((uint32_t)(fabsf(u10) <= L) << 1) |

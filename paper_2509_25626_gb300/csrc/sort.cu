@@ -390,7 +390,10 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
             cnt += c;
         }
     }
-    if (digit_thread) publish_aggregate(state + t, blk, kBins, cnt);
+    // a digit that no element of the whole array carries needs no look-back:
+    // every block skips its word, and no element asks for its base
+    const bool live = digit_thread && digit_total != 0u;
+    if (live) publish_aggregate(state + t, blk, kBins, cnt);
     uint32_t tot;
     const uint32_t dst = block_exclusive_scan(cnt, sm.scratch, &tot);
     const uint32_t dbase = block_exclusive_scan(digit_thread ? digit_total : 0u, sm.scratch, &tot);
@@ -427,7 +430,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
     }
     // base[d]: global position of the block's first digit-d element, less its
     // position in the block (mod 2^32), so that element j goes to base[d] + j
-    if (digit_thread) sm.base[t] = dbase + (uint32_t)walk_back<WIN>(state + t, blk, kBins, cnt, hdr) - dst;
+    if (digit_thread) sm.base[t] = dbase + (live ? (uint32_t)walk_back<WIN>(state + t, blk, kBins, cnt, hdr) : 0u) - dst;
     __syncthreads();
     constexpr int kHalf = IPT / 2;
 #pragma unroll

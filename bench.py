@@ -501,7 +501,7 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "render_traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_sha("render.cu"):
+        if tr.get("workload") == args.workload and tr.get("kernel_source_sha") == kernel_sha("render.cu", "common.cuh"):
             traffic = tr.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -802,11 +802,14 @@ def measure_backward(gs, dev, steps: int, warmup: int):
                 note="forward + backward through gs.rasterize (one host sync per forward for the sort's M)")
 
 
-def kernel_sha(name: str) -> str:
+def kernel_sha(*names: str) -> str:
+    """First 16 hex digits of the SHA-256 of the named csrc files, in order."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2509_25626_gb300", "csrc", name)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2509_25626_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":

@@ -713,13 +713,23 @@ def measure_multiview(gs, dev, steps: int = 5):
             t_render += b.elapsed_time(c)
         res[name] = dict(render_ms=t_render / steps, preprocess_sort_ms=t_front / steps,
                          views_per_s=len(cams) * 1000.0 / ((t_front + t_render) / steps))
-    lens, cycs = [], []
+    lens, cycs, evals = [], [], 0
     for r, cam in zip(rs, cams):
         rg = r.ranges.to(torch.int64)
         lens.append((rg[:, 1] - rg[:, 0]).cpu())
-        cycs.append(gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)[4].reshape(-1).cpu())
+        wl_out = gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)
+        evals += int(wl_out[3].to(torch.int64).sum().item())
+        cycs.append(wl_out[4].reshape(-1).cpu())
     lens = torch.cat(lens).float()
     tc = tile_cycle_stats(torch.cat(cycs))
+    # the renders' roofline: Gaussian-pixel evaluations of the 8 views (the
+    # untimed workload render above) x FLOP_PER_EVAL over the FP32 issue peak
+    peaks = measured_peaks()
+    fp32_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 256 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    for v in res.values():
+        v["tflops"] = evals * FLOP_PER_EVAL / (v["render_ms"] / 1000.0) / 1e12
+        v["frac"] = v["tflops"] / fp32_peak
+    res["evals"] = evals
     return dict(workload="slab_6m_3840x2160x8", gaussians=st.n, views=len(cams), tiles=int(tiles),
                 instances_mean=float(sum(ms) / len(ms)), tile_list_mean=float(lens.mean()),
                 tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), tile_cycles=tc, **res)

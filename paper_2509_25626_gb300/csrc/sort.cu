@@ -353,13 +353,14 @@ struct SweepSmemT {
 };
 using SweepSmem = SweepSmemT<kThreads>;
 
-template <bool kFinal, int NT, int WIN, int ITEMS, typename ValFn>
+template <bool kFinal, int NT, int WIN, int ITEMS, bool kRect, typename ValFn>
 __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const uint32_t (&key)[ITEMS / NT], ValFn val,
                                              uint32_t start, uint32_t n, uint32_t blk, int shift,
                                              uint32_t digit_total, uint64_t *__restrict__ state, SortHeader *hdr,
                                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                              uint64_t *__restrict__ kout64, const uint32_t *__restrict__ depthv,
-                                             int shift_y, uint32_t tiles_x) {
+                                             int shift_y, uint32_t tiles_x, const uint2 *__restrict__ rect_in,
+                                             uint2 *__restrict__ rect_out) {
     constexpr int IPT = ITEMS / NT;
     const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const bool digit_thread = t < (unsigned)kBins;  // thread t < 256 owns digit t
@@ -456,6 +457,16 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
                     kout64[gp[k]] = ((uint64_t)tile << 32) | dv[kFinal ? h * kHalf + k : 0];
                     vout[gp[k]] = vv[k];
                 }
+        } else if (kRect) {  // each value's rectangle instead of its key
+            uint2 rc[kHalf];
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) rc[k] = gp[k] < n ? rect_in[vv[k]] : make_uint2(0u, 0u);
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k)
+                if (gp[k] < n) {
+                    rect_out[gp[k]] = rc[k];
+                    vout[gp[k]] = vv[k];
+                }
         } else {
 #pragma unroll
             for (int k = 0; k < kHalf; ++k)
@@ -470,7 +481,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
 // One pass over (key, value) arrays in device memory, ITEMS elements per
 // block of NT threads.  diff_hist: the digit totals are given as a
 // difference array (the tile passes).
-template <bool kFinal, int NT, int WIN, int ITEMS>
+template <bool kFinal, int NT, int WIN, int ITEMS, bool kRect = false>
 __global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3)) onesweep_kernel(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -480,7 +491,8 @@ __global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3))
                                                             const uint32_t *__restrict__ digit_total, bool diff_hist,
                                                             uint64_t *__restrict__ state, uint32_t *__restrict__ ctr,
                                                             SortHeader *__restrict__ hdr, int shift_y,
-                                                            uint32_t tiles_x) {
+                                                            uint32_t tiles_x, const uint2 *__restrict__ rect_in = nullptr,
+                                                            uint2 *__restrict__ rect_out = nullptr) {
     constexpr int IPT = ITEMS / NT;
     __shared__ SweepSmemT<NT, ITEMS> sm;
     __shared__ uint32_t s_slot;
@@ -501,8 +513,8 @@ __global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3))
         dt += block_exclusive_scan(dt, sm.scratch, &tot);
     }
     auto val = [&](int k) { return (wbase + k * 32 < n) ? vin[wbase + k * 32] : 0u; };
-    rank_scatter<kFinal, NT, WIN, ITEMS>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64, depthv,
-                                   shift_y, tiles_x);
+    rank_scatter<kFinal, NT, WIN, ITEMS, kRect>(sm, key, val, start, n, blk, shift, dt, state, hdr, kout, vout, kout64,
+                                              depthv, shift_y, tiles_x, rect_in, rect_out);
 }
 
 // --- step 3: instance offsets in depth order -----------------------------------
@@ -524,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 3) offsets_kernel(SortWs ws, uint64_
 #pragma unroll
     for (int k = 0; k < kIpt; ++k) {
         const uint32_t i = wbase + k * 32;
-        const uint2 rc = i < n ? ws.rectv[ws.dval[0][i]] : make_uint2(0u, 0u);
+        const uint2 rc = i < n ? ws.srect[i] : make_uint2(0u, 0u);
         tt[k] = ((rc.y & 0xffffu) - (rc.x & 0xffffu)) * ((rc.y >> 16) - (rc.x >> 16));
     }
     // per k: this lane's exclusive prefix within the warp's 32 elements, and
@@ -558,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 3) offsets_kernel(SortWs ws, uint64_
                  b * kSortTileItems < pos + tt[k] && b <= nsweep; ++b)
                 ws.dup_start[b] = i;
             if (pos + tt[k] > m_cap) {  // overflow: uncount the dropped instances
-                const uint2 rc = ws.rectv[ws.dval[0][i]];
+                const uint2 rc = ws.srect[i];
                 const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
                 const uint32_t kept = pos >= m_cap ? 0u : (uint32_t)(m_cap - pos);
                 const uint32_t w = x1 - x0, rows = kept / w, part = kept % w;
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
     for (uint32_t j = t; j < cnt; j += kThreads) {
         const uint32_t p = s_lo + j;
         const uint32_t g = ws.dval[0][p];
-        const uint2 rc = ws.rectv[g];
+        const uint2 rc = ws.srect[p];
         sm.gen.off[j] = ws.offs[p];
         sm.gen.rect[j] = rc.x;
         sm.gen.w[j] = (uint16_t)((rc.y & 0xffffu) - (rc.x & 0xffffu));
@@ -682,8 +694,9 @@ __global__ void __launch_bounds__(kThreads, 3) dup_sweep_kernel(SortWs ws, TileK
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) sm.sweep.wcnt[w][t] = 0;
     __syncthreads();
-    rank_scatter<kFinal, kThreads, kTileWin, kSortTileItems>(sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
-                         ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x);
+    rank_scatter<kFinal, kThreads, kTileWin, kSortTileItems, false>(
+        sm.sweep, key, [&](int k) { return sm.sweep.vals[pw + k * 32]; }, q0, m, blk, 0, digit_total,
+        ws.tile_state[0], ws.hdr, kout, vout, kout64, ws.depthv, tl.shift_y, tiles_x, nullptr, nullptr);
 }
 
 // --- step 6: ranges ----------------------------------------------------------
@@ -731,11 +744,17 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     const uint32_t nb = (uint32_t)sort_blocks_for((uint64_t)n);
     compact_kernel<<<nb, kThreads, 0, st>>>(splats, n, ws, tl);
     const uint32_t nbd = (uint32_t)depth_blocks_for((uint64_t)n);
-    for (int p = 0; p < 4; ++p)
+    // the last pass writes each sorted splat's rectangle in place of its key
+    // (no later step reads the sorted depth bits), so that the offsets and
+    // the duplication read rectangles densely instead of gathering them by id
+    for (int p = 0; p < 3; ++p)
         onesweep_kernel<false, kSweepThreads, kDepthWin, kDepthItems><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
                                                          ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
                                                          ws.hist_depth + kBins * p, false, ws.depth_state[p],
                                                          &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
+    onesweep_kernel<false, kSweepThreads, kDepthWin, kDepthItems, true><<<nbd, kSweepThreads, 0, st>>>(
+        ws.dkey[1], ws.dval[1], nullptr, ws.dval[0], nullptr, nullptr, &ws.hdr->nvis, 24, ws.hist_depth + kBins * 3,
+        false, ws.depth_state[3], &ws.hdr->tile_ctr[kCtrDepth + 3], ws.hdr, 0, 0u, ws.rectv, ws.srect);
     offsets_kernel<<<nb, kThreads, 0, st>>>(ws, m_cap, tl);
     return cudaGetLastError();
 }

@@ -34,6 +34,7 @@ struct SortWs {
     uint32_t *dkey[2], *dval[2];        // depth sort ping-pong, [n]
     uint32_t *depthv;                   // FP32 depth bits by Gaussian id, [n]
     uint2 *rectv;                       // tile rectangle (lo, hi words) by Gaussian id, [n]
+    uint2 *srect;                       // tile rectangle of each depth-sorted splat, [n]
     uint32_t *offs;                     // first instance of each depth-sorted splat, [n]
     uint32_t *dup_start;                // depth-sorted splat holding each tile-pass block's first instance
     uint32_t *tkey, *tval;              // tile sort buffer, [m_cap] each
@@ -114,6 +115,7 @@ inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, uint64_t num_t
     }
     w.depthv = reinterpret_cast<uint32_t *>(take(4 * nn));
     w.rectv = reinterpret_cast<uint2 *>(take(8 * nn));
+    w.srect = reinterpret_cast<uint2 *>(take(8 * nn));
     w.offs = reinterpret_cast<uint32_t *>(take(4 * nn));
     w.dup_start = reinterpret_cast<uint32_t *>(take(4 * (sort_blocks_for(mc) + 2)));
     w.tkey = reinterpret_cast<uint32_t *>(take(4 * mc));

@@ -144,14 +144,6 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid) {
     return m;
 }
 
-// Adds `count` to bin `d` of a shared histogram once per distinct value in
-// the warp (every lane must call; d = ~0u means "nothing to add").
-__device__ __forceinline__ void warp_hist_add(uint32_t *hist, uint32_t d) {
-    const bool valid = d != 0xffffffffu;
-    const unsigned peers = digit_peers(d, valid);
-    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
-}
-
 // Exclusive prefix of `blk` for a scan: publish this block's aggregate, then
 // sum every predecessor's aggregate with the whole block (coalesced, one
 // round trip per 256 predecessors).  No prefix chain is formed, so blocks
@@ -302,6 +294,7 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
             ws.rectv[g] = make_uint2(r4[k].z, r4[k].w);
             atomicAdd(&s_hist[warp][0][d & 0xffu], 1u);
             atomicAdd(&s_hist[warp][1][(d >> 8) & 0xffu], 1u);
+            atomicAdd(&s_hist[warp][2][(d >> 16) & 0xffu], 1u);
             const uint32_t x0 = r4[k].z & 0xffffu, y0 = r4[k].z >> 16, x1 = r4[k].w & 0xffffu, y1 = r4[k].w >> 16;
             if (small_grid) {  // one byte per coordinate: digit = tx, then ty, no wrap
                 atomicAdd(&s_tdiff[0][x0], y1 - y0);
@@ -315,9 +308,13 @@ __global__ void __launch_bounds__(kThreads, 3) compact_kernel(const gs_splat *__
             }
         }
         pos += (uint32_t)__popc(bal[k]);
-        // the two high bytes take few distinct values: aggregate them per warp
-        warp_hist_add(s_hist[warp][2], vis ? ((d >> 16) & 0xffu) : 0xffffffffu);
-        warp_hist_add(s_hist[warp][3], vis ? (d >> 24) : 0xffffffffu);
+        // the high byte takes few distinct values (the exponent range): one
+        // atomic per distinct value in the warp
+        {
+            const uint32_t d3 = vis ? (d >> 24) : 0x100u;
+            const unsigned pm = __match_any_sync(0xffffffffu, d3);
+            if (vis && (pm & lt) == 0u) atomicAdd(&s_hist[warp][3][d3], (uint32_t)__popc(pm));
+        }
     }
     if (blk == gridDim.x - 1 && threadIdx.x == 0) ws.hdr->nvis = (uint32_t)(excl + total);
     __syncthreads();

@@ -38,15 +38,15 @@ constexpr float kLn2 = 0.6931471805599453f;
 struct __align__(16) StagedA { float x, y, w00, w01; };
 struct __align__(16) StagedB { float w11, lg2o, r, g; };
 
-// Sums 16 per-lane values over the warp with 16 shuffles instead of 16 x 5:
-// at each of the offsets 16, 8, 4, 2 a lane keeps one half of its values
-// (the upper half if its offset bit is set), adds its partner's copy of that
-// half, and passes the other half on; offset 1 finishes.  On return v[0] is
-// the warp sum of value 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of the lane),
-// the same in both lanes of each pair.
-__device__ __forceinline__ float warp_sum16(float (&v)[16], unsigned lane) {
+// Sums 8 per-lane values over the warp with 7 shuffles instead of 8 x 5: at
+// each of the offsets 16, 8, 4 a lane keeps one half of its values (the
+// upper half if its offset bit is set), adds its partner's copy of that half
+// and passes the other half on; offsets 2 and 1 finish.  On return v[0] is
+// the warp sum of value 4 b4 + 2 b3 + b2 (b_i = bit i of the lane), that is
+// of value lane >> 2, the same in the four lanes of each group.
+__device__ __forceinline__ float warp_sum8(float (&v)[8], unsigned lane) {
 #pragma unroll
-    for (int n = 16, off = 16; n > 1; n >>= 1, off >>= 1) {
+    for (int n = 8, off = 16; n > 1; n >>= 1, off >>= 1) {
         const bool hi = (lane & (unsigned)off) != 0u;
 #pragma unroll
         for (int i = 0; i < n / 2; ++i) {
@@ -55,7 +55,14 @@ __device__ __forceinline__ float warp_sum16(float (&v)[16], unsigned lane) {
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
 }
 
 struct PixelBack {
@@ -195,16 +202,22 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
             const float u1 = u0 - sa.w00;
             const float v = sb.w11 * dy;
             const float vv = fmaf(-v, v, sb.lg2o);
-            float acc[16];
+            float acc[kNGrad];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+            for (int k = 0; k < kNGrad; ++k) acc[k] = 0.f;
             back_pixel(p0, pos, u0, v, dx0, dy, fmaf(-u0, u0, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, inv_o, acc);
             back_pixel(p1, pos, u1, v, dx1, dy, fmaf(-u1, u1, vv), sa.w00, sa.w01, sb.w11, sb.r, sb.g, b, inv_o, acc);
             const bool any = acc[6] != 0.f || acc[7] != 0.f || acc[8] != 0.f || acc[5] != 0.f || acc[0] != 0.f;
             if (__any_sync(0xffffffffu, any)) {
-                const float sum = warp_sum16(acc, lane);
-                const unsigned slot = lane >> 1;  // 8 b4 + 4 b3 + 2 b2 + b1
-                if ((lane & 1u) == 0u && slot < (unsigned)kNGrad) atomicAdd(&s_grad[j][slot], sum);
+                // values 0-7 by halving (lane group lane >> 2 holds value lane >> 2),
+                // value 8 by a plain butterfly; one shared atomic per value
+                float v8[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v8[k] = acc[k];
+                const float sum = warp_sum8(v8, lane);
+                const float sum8 = warp_sum(acc[8]);
+                const bool first = (lane & 3u) == 0u;
+                if (first || lane == 1u) atomicAdd(&s_grad[j][first ? lane >> 2 : 8u], first ? sum : sum8);
             }
         }
         __syncthreads();

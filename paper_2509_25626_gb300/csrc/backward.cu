@@ -261,13 +261,41 @@ __global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
     __shared__ float s_sh[kPreBackThreads][kShStride];
     const int64_t g0 = (int64_t)blockIdx.x * kPreBackThreads;
     const int nb = (int)min((int64_t)kPreBackThreads, n - g0);  // Gaussians of this block
-    for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) s_sh[f / 48][f % 48] = sh[g0 * 48 + f];
+    // full blocks with 16-byte aligned SH arrays move them as float4, all 12
+    // loads of a thread in flight at once
+    const bool vec = nb == kPreBackThreads &&
+                     ((reinterpret_cast<uintptr_t>(sh) | reinterpret_cast<uintptr_t>(dsh)) & 15u) == 0u;
+    if (vec) {
+        const float4 *src = reinterpret_cast<const float4 *>(sh + g0 * 48);
+        float4 v[12];
+#pragma unroll
+        for (int r = 0; r < 12; ++r) v[r] = __ldg(src + threadIdx.x + r * kPreBackThreads);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int f = 4 * ((int)threadIdx.x + r * kPreBackThreads), row = f / 48, col = f % 48;
+            s_sh[row][col] = v[r].x;
+            s_sh[row][col + 1] = v[r].y;
+            s_sh[row][col + 2] = v[r].z;
+            s_sh[row][col + 3] = v[r].w;
+        }
+    } else {
+        for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) s_sh[f / 48][f % 48] = sh[g0 * 48 + f];
+    }
     __syncthreads();
     const int64_t gi = g0 + threadIdx.x;
     if (gi < n) preprocess_backward_one(means, log_scales, quats, logits, s_sh[threadIdx.x], gi, sh_degree, cam,
                                         splats, dsplat, dmeans, dlog_scales, dquats, dlogits);
     __syncthreads();
-    for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) dsh[g0 * 48 + f] = s_sh[f / 48][f % 48];
+    if (vec) {
+        float4 *dst = reinterpret_cast<float4 *>(dsh + g0 * 48);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int f4 = (int)threadIdx.x + r * kPreBackThreads, f = 4 * f4, row = f / 48, col = f % 48;
+            dst[f4] = make_float4(s_sh[row][col], s_sh[row][col + 1], s_sh[row][col + 2], s_sh[row][col + 3]);
+        }
+    } else {
+        for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) dsh[g0 * 48 + f] = s_sh[f / 48][f % 48];
+    }
 }
 
 // One Gaussian of preprocess_backward_kernel; shg: its 48 SH coefficients,

@@ -492,10 +492,11 @@ def main():
     render_tflops = evals_mean * FLOP_PER_EVAL / (rend_ms / 1000.0) / 1e12
     # preprocess bytes: every Gaussian's mean; scales and rotation of those
     # in front of the near plane; opacity and SH of the visible ones (culled
-    # Gaussians need neither); the record and the dense sort inputs out
+    # Gaussians need neither); out, the whole record of a visible Gaussian,
+    # the last 32 bytes of a culled one's, and every dense sort input
     front_mean = statistics.mean(front[p] for p in used)
     vis_mean = statistics.mean(vis[p] for p in used)
-    pre_bytes = n * 12 + front_mean * 28 + vis_mean * (4 + 192) + n * (64 + 16)
+    pre_bytes = n * 12 + front_mean * 28 + vis_mean * (4 + 192) + vis_mean * 64 + (n - vis_mean) * 32 + n * 16
     pre_gbs = pre_bytes / (pre_ms / 1000.0) / 1e9
     traffic = None
     try:

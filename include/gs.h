@@ -82,7 +82,9 @@ typedef struct gs_scene {
  * |dx| <= cull_hx, |dy| <= cull_hy the splat is skipped for every pixel (the
  * bound is the ellipse's bounding box, widened by 2^-10 relative + 1/64
  * pixel to absorb FP32 rounding); both are negative if alpha < 1/255
- * everywhere.  A culled Gaussian has radius = 0 and tiles_touched = 0. */
+ * everywhere.  A culled Gaussian has radius = 0, tiles_touched = 0, an
+ * empty rectangle, negative cull_hx / cull_hy and its depth; gs_preprocess
+ * leaves its other fields (x .. g) unwritten, since it is in no tile list. */
 typedef struct gs_splat {
     float x, y;               /* pixel-space mean */
     float w00, w01, w11;      /* inverse-covariance factor (see above) */

@@ -37,10 +37,10 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
     return dop + err;
 }
 
+// A culled Gaussian appears in no tile list, so nothing reads its first 32
+// bytes: only the radius, the empty cull box and the sort inputs are written.
 __device__ __forceinline__ void write_culled(gs_splat *out, uint4 *sort_in, float depth) {
     float4 *o = reinterpret_cast<float4 *>(out);
-    o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     o[2] = make_float4(0.f, -1.f, -1.f, 0.f);     // b, cull box empty, radius = 0
     o[3] = make_float4(depth, 0.f, 0.f, 0.f);     // depth, tiles = 0, rect 0
     *sort_in = make_uint4(__float_as_uint(depth), 0u, 0u, 0u);

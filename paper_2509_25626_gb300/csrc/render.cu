@@ -144,7 +144,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
         for (uint32_t q8 = 0; q8 < cnt; q8 += 8) {
             if (__all_sync(0xffffffffu, p0.done && p1.done)) break;  // warp-uniform
             const uint32_t qe = min(cnt, q8 + 8u);
-#pragma unroll 2
+#pragma unroll 4
             for (uint32_t q = q8; q < qe; ++q) {
                 const uint32_t j = s_list[warp][q];
                 const StagedA sa = s_a[j];

@@ -55,6 +55,11 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
                                                          uint4 *__restrict__ sort_in) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
+    // the rotation, scales and opacity of a Gaussian that survives the
+    // near-plane test are needed next: start them towards L2 with the mean
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(quats + g));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(log_scales + 3 * g));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(logits + g));
     const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
     const float *V = cam.V;
 

@@ -58,8 +58,8 @@ constexpr float kLog2_255 = 7.994353436858858f;
 // here and in the render (|w| <= ~1.6 after the 0.3 dilation and |d| within
 // a few thousand pixels put it near 1e-3).  The band removes the quarters
 // the box keeps only because the ellipse is thin and slanted.
-__device__ __forceinline__ uint32_t quarter_mask(const float4 a, const float4 b, const float4 c, float tx0,
-                                                 float ty0) {
+__host__ __device__ __forceinline__ uint32_t quarter_mask(const float4 a, const float4 b, const float4 c,
+                                                          float tx0, float ty0) {
     if (!(c.y >= 0.f)) return 0u;  // alpha < 1/255 everywhere (empty box)
     // coordinates relative to the tile's first pixel (the slack in hx, hy
     // and R covers the rounding of these differences)

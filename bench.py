@@ -43,6 +43,7 @@ def parse_args():
     p.add_argument("--no-backward", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-multiview", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the 16k-Gaussian 256x256 frame rate")
     p.add_argument("--inflight", type=int, default=3, help="frames in flight on separate streams")
     p.add_argument("--cpu-rows", type=int, default=4, help="tile rows the oracle renders per sampled frame")
     p.add_argument("--profile-frames", type=int, default=0,
@@ -554,6 +555,9 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = measure_serving(gs, dev)
 
+    small = None
+    if rank == 0 and not args.no_small:
+        small = measure_small_config(gs, dev)
     multiview = None
     if rank == 0 and not args.no_multiview:
         multiview = measure_multiview(gs, dev)
@@ -586,7 +590,7 @@ def main():
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
             roofline=roofline, frame_roofline=frame_roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
             e2e_resident_scene=e2e_resident,
-            serving=serving, multiview=multiview,
+            serving=serving, multiview=multiview, small_config=small,
             backward=backward,
             gpu_launches=launches_per_frame * args.steps, clocks=clocks,
             peaks_src=peaks["src"],
@@ -641,6 +645,38 @@ def measure_serving(gs, dev, rate: float = 200.0, duration: float = 2.5):
                scenes={name: n for name, n, _ in specs}, resolutions=[f"{w}x{h}" for w, h in res],
                batches=int(srv.stats["batches"]), overflow_or_timeout=int(srv.stats["overflow_or_timeout"]))
     return out
+
+
+def measure_small_config(gs, dev, frames: int = 500):
+    """The 16,384-Gaussian 256x256 frame (its one pose): whole frames
+    (preprocess, sort, render) one after another on one stream, CUDA events
+    around them.  Its 3.9 MB scene stays in L2 between frames (not flushed):
+    a frame this small is bound by launch and latency, not by HBM."""
+    import torch
+    from synth import CONFIGS
+    wl = CONFIGS["fwd_16k_256"]
+    scene, cam = wl["scene"](), wl["cameras"]()[0]
+    st = gs.SceneTensors.from_scene(scene, dev)
+    sp = gs.preprocess(st, cam)
+    _, _, _, m, _ = gs.sort(sp, scene.n, cam, 1 << 22)
+    del sp
+    r = gs.Renderer(scene.n, cam.width, cam.height, int(m * 1.05) + 4096, dev)
+    for _ in range(10):
+        r.frame(st, cam)
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(frames):
+        r.frame(st, cam)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / frames
+    ne = gs.render_workload(r.splats, r.vals, r.ranges, cam)[3]
+    evals = int(ne.to(torch.int64).sum().item())
+    return dict(workload="fwd_16k_256", gaussians=scene.n, width=cam.width, height=cam.height, frames=frames,
+                instances=int(m), ms_per_frame=ms, frames_per_s=1000.0 / ms, evals=evals,
+                evals_per_s=evals / (ms / 1000.0), l2="scene resident in L2 between frames (3.9 MB)")
 
 
 def measure_multiview(gs, dev, steps: int = 5):

@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) render_backward_kernel(
             wcnt += __popc(bal);
         }
         __syncwarp();
+#pragma unroll 4
         for (int q = (int)wcnt - 1; q >= 0; --q) {
             const uint32_t j = s_list[warp][q];
             const uint32_t pos = start + j + 1;

@@ -9,7 +9,8 @@
 //                the tile sort (the latter from rectangle corners alone)
 //                                                           (one look-back scan)
 //   2. depth     stable LSD radix sort of (depth bits, id) over the visible
-//                splats, 4 x 8-bit passes                   (one kernel per pass)
+//                splats, 4 x 8-bit passes; the last writes each sorted
+//                splat's rectangle beside its id            (one kernel per pass)
 //   3. offsets   exclusive scan of tiles_touched in depth order -> M and each
 //                splat's first instance                     (one look-back scan)
 //   4. dup+tile  instances generated in (depth, id, row-major tile) order,

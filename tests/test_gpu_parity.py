@@ -62,6 +62,10 @@ def scenes_small():
     # slanted band) may leave out only splats below 1/255 on a whole quarter
     sc, cam = needle_scene(3000, 21, 200, 150)
     out.append(("needles3k_200x150", sc, cam))
+    # few large splats just past the near plane, some centred off screen:
+    # radii of hundreds of pixels, so culling and blending far from the mean
+    sc, cam = tiny_scene(60, 31, 160, 120, z_range=(0.25, 1.5), log_scale=(-3.0, 1.0), spill=1.6)
+    out.append(("nearlarge60_160x120", sc, cam))
     return out
 
 

@@ -681,9 +681,10 @@ def measure_small_config(gs, dev, frames: int = 500):
 
 def measure_multiview(gs, dev, steps: int = 5):
     """Load-imbalance workload: 6M Gaussians, half packed in an occluding
-    slab, 8 views at 3840x2160.  Per step: the 8 views' preprocess and sort,
-    then their renders in ONE persistent launch (gs_render_batch); compared
-    with the same renders as 8 separate gs_render launches."""
+    slab, 8 views at 3840x2160.  Per step: the 8 views' preprocess and sort
+    (one stream per view), then their renders in ONE persistent launch
+    (gs_render_batch); compared with the same renders as 8 separate
+    gs_render launches."""
     import ctypes
     import torch
     from paper_2509_25626_gb300 import _lib as L
@@ -718,10 +719,22 @@ def measure_multiview(gs, dev, steps: int = 5):
     stream = torch.cuda.current_stream(dev)
     sptr = ctypes.c_void_p(int(stream.cuda_stream))
 
+    # each view's preprocess and sort on a stream of its own (the views are
+    # independent and their sorts are latency-bound), forked from and joined
+    # to the timing stream
+    view_streams = [torch.cuda.Stream(dev) for _ in cams]
+
     def front():
-        for r, cam in zip(rs, cams):
-            gs.preprocess(st, cam, r.splats)
-            gs.sort(r.splats, st.n, cam, r.m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for vs, r, cam in zip(view_streams, rs, cams):
+            vs.wait_event(fork)
+            gs.preprocess(st, cam, r.splats, stream=vs)
+            gs.sort(r.splats, st.n, cam, r.m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False, stream=vs)
+        for vs in view_streams:
+            join = torch.cuda.Event()
+            join.record(vs)
+            stream.wait_event(join)
 
     def batched():
         L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
@@ -750,6 +763,32 @@ def measure_multiview(gs, dev, steps: int = 5):
             t_render += b.elapsed_time(c)
         res[name] = dict(render_ms=t_render / steps, preprocess_sort_ms=t_front / steps,
                          views_per_s=len(cams) * 1000.0 / ((t_front + t_render) / steps))
+
+    # pipelined: each view's preprocess, sort and render on its own stream,
+    # so one view's render overlaps the others' sorts (whole step timed)
+    def pipelined():
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for vs, r, cam in zip(view_streams, rs, cams):
+            vs.wait_event(fork)
+            gs.preprocess(st, cam, r.splats, stream=vs)
+            gs.sort(r.splats, st.n, cam, r.m_cap, r.keys, r.vals, r.ranges, r.workspace, count=False, stream=vs)
+            gs.render(r.splats, r.vals, r.ranges, cam, (0.0, 0.0, 0.0), r.image, r.final_T, r.n_contrib, stream=vs)
+        for vs in view_streams:
+            join = torch.cuda.Event()
+            join.record(vs)
+            stream.wait_event(join)
+
+    pipelined()
+    torch.cuda.synchronize(dev)
+    a, b = E(), E()
+    a.record(stream)
+    for _ in range(steps):
+        pipelined()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    step_ms = a.elapsed_time(b) / steps
+    pipe = dict(step_ms=step_ms, views_per_s=len(cams) * 1000.0 / step_ms)
     lens, cycs, evals = [], [], 0
     for r, cam in zip(rs, cams):
         rg = r.ranges.to(torch.int64)
@@ -767,6 +806,7 @@ def measure_multiview(gs, dev, steps: int = 5):
         v["tflops"] = evals * FLOP_PER_EVAL / (v["render_ms"] / 1000.0) / 1e12
         v["frac"] = v["tflops"] / fp32_peak
     res["evals"] = evals
+    res["pipelined"] = pipe
     return dict(workload="slab_6m_3840x2160x8", gaussians=st.n, views=len(cams), tiles=int(tiles),
                 instances_mean=float(sum(ms) / len(ms)), tile_list_mean=float(lens.mean()),
                 tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), tile_cycles=tc, **res)

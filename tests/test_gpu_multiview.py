@@ -90,3 +90,78 @@ def test_batch_job_table_sizes(n_jobs):
     for c, bg, sp, v, r, ref, out in jobs:
         for a, b in zip(out, ref):
             assert torch.equal(a, b)
+
+
+def test_full_size_slab_views_sampled(oracle):
+    """The load-imbalance workload at full size -- 6M Gaussians, half of them
+    in the occluding slab, 3840x2160 -- with two of its views rendered in one
+    gs_render_batch launch as the benchmark does: the batch equals each
+    view's own frame bit for bit, the first view's sort has the properties a
+    sort has at any size, and the tile rows through the slab (the longest
+    lists) match the oracle.  The oracle sorts only the instances of those
+    rows: each Gaussian's rectangle clipped to them leaves their tiles' lists
+    and order unchanged."""
+    from paper_2509_25626_gb300 import SPLAT_DTYPE
+    from parity import (POS_EPS_E2E, TAU_ALPHA, TAU_T, ambiguous_gaussians, check_sorted_output, compare_images,
+                        flip_tile_mask, rect_of)
+    sc = slab_scene(6_000_000, seed=5)
+    st = gs.SceneTensors.from_scene(sc, "cuda")
+    cams = [orbit_camera(k, 8, 4.0, 3840, 2160, arc=np.radians(40.0)) for k in (0, 7)]
+    rs = []
+    for cam in cams:
+        r = gs.Renderer(sc.n, cam.width, cam.height, 90_000_000)
+        r.frame(st, cam)
+        m, over = r.instances()
+        assert not over
+        rs.append((r, m))
+    outs = [tuple(torch.empty_like(t) for t in (r.image, r.final_T, r.n_contrib)) for r, _ in rs]
+    srv = S.Server({}, max_batch=2)
+
+    class _Req:
+        def __init__(self, cam):
+            self.cam, self.bg = cam, (0.0, 0.0, 0.0)
+
+    class _Slot:
+        def __init__(self, r, out, cam):
+            self.splats, self.vals, self.ranges = r.splats, r.vals, r.ranges
+            self.image, self.final_T, self.n_contrib = out
+            self.tiles = gs.num_tiles(cam)
+
+    srv._write_desc([(_Req(c), _Slot(r, o, c)) for c, (r, _), o in zip(cams, rs, outs)])
+    srv.desc_dev.copy_(srv.desc_host)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
+                                    ctypes.c_void_p(srv.counter.data_ptr()), 0, stream), "gs_render_batch")
+    torch.cuda.synchronize()
+    for (r, _), out in zip(rs, outs):
+        for a, b in zip(out, (r.image, r.final_T, r.n_contrib)):
+            assert torch.equal(a, b)
+
+    cam, (r, m) = cams[0], rs[0]
+    recs = r.splats.cpu().numpy().view(SPLAT_DTYPE).reshape(-1)[: sc.n]
+    check_sorted_output(r.keys.cpu().numpy(), r.vals.cpu().numpy(), r.ranges.cpu().numpy(), m, recs, cam.tiles_x)
+    lens = r.ranges.cpu().numpy().astype(np.int64)
+    ty0, ty1 = 66, 68  # tile rows through the slab
+    rows = (16 * ty0, 16 * ty1)
+    band_lens = (lens[:, 1] - lens[:, 0]).reshape(cam.tiles_y, cam.tiles_x)[ty0:ty1]
+    assert band_lens.max() > 50 * max(1.0, float((lens[:, 1] - lens[:, 0]).mean()))  # the heavy tiles
+
+    pre = oracle.preprocess(sc, cam)
+    clip = dict(pre)
+    rect = pre["rect"].copy()
+    rect[:, 1] = np.maximum(rect[:, 1], ty0)
+    rect[:, 3] = np.minimum(rect[:, 3], ty1)
+    keep = (pre["tiles"] > 0) & (rect[:, 3] > rect[:, 1])
+    clip["rect"] = np.where(keep[:, None], rect, 0).astype(np.int32)
+    clip["tiles"] = np.where(keep, (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0).astype(np.int32)
+    srt = oracle.duplicate_sort(clip, cam)
+    img = oracle.render(clip, srt, cam, tau_alpha=TAU_ALPHA, tau_T=TAU_T, rows=rows, pos_eps=POS_EPS_E2E)
+    sl = slice(*rows)
+    band = {k: (v[:, sl] if k == "color" else v[sl]) for k, v in img.items()}
+    flips = np.nonzero((recs["tiles_touched"].astype(np.int64) != pre["tiles"]) |
+                       np.any(rect_of(recs) != pre["rect"], axis=1))[0]
+    assert np.all(ambiguous_gaussians(pre, cam)[flips]), "a rectangle flipped on a non-ambiguous Gaussian"
+    amb = flip_tile_mask(recs, pre, flips, cam, rows=rows)
+    rep = compare_images(outs[0][0].cpu().numpy()[:, sl], outs[0][1].cpu().numpy()[sl],
+                         outs[0][2].cpu().numpy()[sl], band, exclude=amb, max_excluded_frac=0.03)
+    print("slab full size", m, int(band_lens.max()), rep)

@@ -120,3 +120,35 @@ def test_quarter_mask_never_drops_a_kept_pixel(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     print(out.stdout)
     assert out.returncode == 0 and out.stdout.strip().endswith("OK"), out.stdout
+
+
+# Plausible mistakes in the mask, each of which must make the check above
+# fail (so the check can see them): a band half-width without the w01 term,
+# the wrong sign of a quarter-centre step, quarter centres off by half a
+# pixel.
+MUTANTS = {
+    "no_w01_half_width": ("3.5f * (fabsf(a.z) + fabsf(a.w))", "3.5f * fabsf(a.z)"),
+    "sign_of_w01_step": ("u01 = fmaf(-8.f, a.w, u00)", "u01 = fmaf(8.f, a.w, u00)"),
+    "centre_shift": ("x - 3.5f", "x - 4.0f"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_quarter_mask_check_catches_mutants(tmp_path, name):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("no nvcc")
+    old, new = MUTANTS[name]
+    with open(os.path.join(CSRC, "common.cuh")) as f:
+        text = f.read()
+    assert text.count(old) == 1, name
+    mdir = tmp_path / "mut"
+    mdir.mkdir()
+    (mdir / "common.cuh").write_text(text.replace(old, new))
+    src = tmp_path / "qm.cu"
+    src.write_text(DRIVER)
+    exe = tmp_path / "qm"
+    subprocess.run([nvcc, "-std=c++17", "-O2", f"-I{mdir}", f"-I{CSRC}", f"-I{INCLUDE}", str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert out.returncode != 0 and "missed 0" not in out.stdout, out.stdout

@@ -49,6 +49,10 @@ def parse_args():
     p.add_argument("--profile-frames", type=int, default=0,
                    help="profiler driver: one sizing sort, then this many frames of pose 0 one after another "
                         "(launch order: preprocess + 9 sort kernels, then 11 kernels per frame); no timing")
+    p.add_argument("--profile-multiview", type=int, default=0,
+                   help="profiler driver: a 2M-Gaussian slab scene (the multi-view recipe at a third of its size), "
+                        "two 1920x1080 views preprocessed and sorted, then this many gs_render_batch launches of "
+                        "both views; no timing")
     p.add_argument("--profile-backward", type=int, default=0,
                    help="profiler driver: forward of the 1M-Gaussian 1237x822 backward workload (pose 0), then this "
                         "many backward passes (per pass: gs_render_backward_splats, gs_preprocess_backward); no "
@@ -262,6 +266,44 @@ def main():
     import paper_2509_25626_gb300 as gs
     from paper_2509_25626_gb300 import _lib as L
     from synth import CONFIGS
+
+    if args.profile_multiview > 0:  # fixed launch sequence for ncu captures
+        import ctypes
+        from paper_2509_25626_gb300 import serve as S
+        from synth import orbit_camera, slab_scene
+        sm_ = slab_scene(2_000_000, seed=5)
+        stm = gs.SceneTensors.from_scene(sm_, dev)
+        cms = [orbit_camera(k, 8, 4.0, 1920, 1080, arc=math.radians(40.0)) for k in (0, 7)]
+        views = []
+        for cm in cms:
+            sp = gs.preprocess(stm, cm)
+            _, vals, ranges, _, _ = gs.sort(sp, sm_.n, cm, 1 << 25)
+            out = (torch.empty((3, cm.height, cm.width), dtype=torch.float32, device=dev),
+                   torch.empty((cm.height, cm.width), dtype=torch.float32, device=dev),
+                   torch.empty((cm.height, cm.width), dtype=torch.int32, device=dev))
+            views.append((cm, sp, vals, ranges, out))
+        srv = S.Server({}, max_batch=len(cms))
+
+        class _Req:
+            def __init__(self, cam):
+                self.cam, self.bg = cam, (0.0, 0.0, 0.0)
+
+        class _Slot:
+            def __init__(self, sp, vals, ranges, out, cam):
+                self.splats, self.vals, self.ranges = sp, vals, ranges
+                self.image, self.final_T, self.n_contrib = out
+                self.tiles = gs.num_tiles(cam)
+
+        srv._write_desc([(_Req(c), _Slot(sp, v, r, o, c)) for c, sp, v, r, o in views])
+        srv.desc_dev.copy_(srv.desc_host)
+        sptr = ctypes.c_void_p(int(torch.cuda.current_stream(dev).cuda_stream))
+        for _ in range(args.profile_multiview):
+            L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
+                                            ctypes.c_void_p(srv.counter.data_ptr()), 0, sptr), "gs_render_batch")
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile_multiview": args.profile_multiview, "workload": "slab_2m_1920x1080x2"}))
+        return 0
 
     if args.profile_backward > 0:  # fixed launch sequence for ncu captures
         wb = CONFIGS["bwd_1m_1237x822"]

@@ -359,12 +359,21 @@ void oracle_duplicate_sort(int64_t n, const int32_t *rect, const int32_t *tiles,
  *                 optional output of the paper's render kernels, Appendix B)
  *   n_eval        Gaussians evaluated before the pixel stopped (the
  *                 "Gaussian-pixel evaluations" work count)
- *   near_count    decisions whose log-space margin is under tau, widened by
- *                 the effect of a relative rounding pos_eps of the splat's
- *                 pixel coordinates (FP32 stores them with |x| ulp ~ |x| 2^-24)
- *   flip_impact   the largest bound, over those near decisions, on how much
- *                 one flipped decision could move any colour channel
+ *   near_count    threshold decisions (alpha < 1/255 skip, T (1 - alpha) <
+ *                 1e-4 stop) whose log-space distance to the threshold is
+ *                 under tau_alpha / tau_T, widened by how far a relative
+ *                 rounding pos_eps of the splat's pixel coordinates can move
+ *                 that distance (FP32 stores them with ulp ~ |x| 2^-24):
+ *                 |d log(alpha) / d x| pos_eps (|x| + 1) + the same for y,
+ *                 times alpha / (1 - alpha) for the stop decision, whose
+ *                 quantity is log(1 - alpha)
+ *   flip_impact   over those near decisions, the largest change of any colour
+ *                 channel when that one decision is taken the other way and
+ *                 the rest of the list is walked again exactly (so a flip
+ *                 that moves a later stop is counted in full)
  * ------------------------------------------------------------------------- */
+enum { DECIDE_ALPHA = 0, DECIDE_STOP = 1 };
+
 typedef struct {
     double color[3];
     double invdepth;
@@ -375,14 +384,36 @@ typedef struct {
     double flip_impact;
 } pixel_t;
 
-static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int64_t len, const double *xy,
-                               const double *conic, const double *opacity, const double *rgb, const double *depth,
-                               const double *bg, double tau_alpha, double tau_T, double pos_eps, double cmax) {
+/* Growable list of near decisions: entry = 2 * list index + kind. */
+typedef struct {
+    int64_t *at;
+    int64_t n, cap;
+    int64_t local[32];
+} near_list_t;
+
+static void near_push(near_list_t *l, int64_t v) {
+    if (l->n == l->cap) {
+        int64_t cap = 2 * l->cap;
+        int64_t *p = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+        memcpy(p, l->at, sizeof(int64_t) * (size_t)l->n);
+        if (l->at != l->local) free(l->at);
+        l->at = p;
+        l->cap = cap;
+    }
+    l->at[l->n++] = v;
+}
+
+/* The walk of one pixel.  flip < 0: as defined.  Otherwise the decision
+ * flip = 2 i + kind (list entry i) is taken the other way: a skipped
+ * Gaussian is blended with its alpha, a blended one skipped; a stop is not
+ * taken, or taken there.  near (may be NULL) collects the near decisions. */
+static pixel_t walk_pixel(double pxf, double pyf, const uint32_t *ids, int64_t len, const double *xy,
+                          const double *conic, const double *opacity, const double *rgb, const double *depth,
+                          const double *bg, double tau_alpha, double tau_T, double pos_eps, int64_t flip,
+                          near_list_t *near) {
     pixel_t out;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0;
-    int32_t contrib = 0, last = 0, near = 0;
-    double impact = 0.0;
-    double bgmax = fmax(bg[0], fmax(bg[1], bg[2]));
+    int32_t contrib = 0, last = 0;
     for (int64_t i = 0; i < len; ++i) {
         uint32_t g = ids[i];
         ++contrib;
@@ -392,21 +423,20 @@ static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int6
         if (power > 0.0) continue;
         double raw = opacity[g] * exp(power);
         double alpha = fmin(ALPHA_MAX, raw);
-        /* margin widened by how far a relative rounding pos_eps of the mean's
-         * coordinates moves log(alpha): |d power / d x_g| pos_eps (|x_g| + 1) */
+        /* |d log(alpha) / d x_g| pos_eps (|x_g| + 1) + the same for y */
         double gx = fabs(a * dx + b * dy), gy = fabs(b * dx + c * dy);
         double pos_err = pos_eps * (gx * (fabs(xy[2 * g]) + 1.0) + gy * (fabs(xy[2 * g + 1]) + 1.0));
-        if (raw > 0.0 && fabs(log(raw) - log(ALPHA_MIN)) < tau_alpha + pos_err) {
-            ++near;
-            impact = fmax(impact, 2.0 * ALPHA_MIN * T * (cmax + bgmax));
-        }
-        if (alpha < ALPHA_MIN) continue;
+        if (near && raw > 0.0 && fabs(log(raw) - log(ALPHA_MIN)) < tau_alpha + pos_err)
+            near_push(near, 2 * i + DECIDE_ALPHA);
+        int skip = alpha < ALPHA_MIN;
+        if (flip == 2 * i + DECIDE_ALPHA) skip = !skip;
+        if (skip) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(log(Tn) - log(T_MIN)) < tau_T + pos_err * alpha / (1.0 - alpha)) {
-            ++near;
-            impact = fmax(impact, T * (cmax + bgmax));
-        }
-        if (Tn < T_MIN) break; /* stop; this Gaussian is not blended */
+        if (near && fabs(log(Tn) - log(T_MIN)) < tau_T + pos_err * alpha / (1.0 - alpha))
+            near_push(near, 2 * i + DECIDE_STOP);
+        int stop = Tn < T_MIN;
+        if (flip == 2 * i + DECIDE_STOP) stop = !stop;
+        if (stop) break; /* stop; this Gaussian is not blended */
         for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * alpha * T;
         D += alpha * T / depth[g];
         T = Tn;
@@ -417,15 +447,30 @@ static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int6
     out.T = T;
     out.n_contrib = last;
     out.n_eval = contrib;
-    out.near_count = near;
-    out.flip_impact = impact;
+    out.near_count = 0;
+    out.flip_impact = 0.0;
     return out;
 }
 
-static double max_rgb(int64_t n, const double *rgb) {
-    double c = 0.0;
-    for (int64_t i = 0; i < 3 * n; ++i) c = fmax(c, rgb[i]);
-    return c;
+static pixel_t composite_pixel(double pxf, double pyf, const uint32_t *ids, int64_t len, const double *xy,
+                               const double *conic, const double *opacity, const double *rgb, const double *depth,
+                               const double *bg, double tau_alpha, double tau_T, double pos_eps) {
+    near_list_t near;
+    near.at = near.local;
+    near.n = 0;
+    near.cap = 32;
+    pixel_t out = walk_pixel(pxf, pyf, ids, len, xy, conic, opacity, rgb, depth, bg, tau_alpha, tau_T, pos_eps, -1,
+                             &near);
+    double impact = 0.0;
+    for (int64_t k = 0; k < near.n; ++k) {
+        pixel_t alt = walk_pixel(pxf, pyf, ids, len, xy, conic, opacity, rgb, depth, bg, 0.0, 0.0, 0.0, near.at[k],
+                                 NULL);
+        for (int ch = 0; ch < 3; ++ch) impact = fmax(impact, fabs(alt.color[ch] - out.color[ch]));
+    }
+    out.near_count = (int32_t)near.n;
+    out.flip_impact = impact;
+    if (near.at != near.local) free(near.at);
+    return out;
 }
 
 static void store_pixel(const pixel_t *p, int64_t pix, int64_t npix, double *out_color, double *invdepth,
@@ -450,7 +495,7 @@ void oracle_render(int width, int height, int row0, int row1, const uint32_t *ra
                    int32_t *n_eval, int32_t *near_count, double *flip_impact) {
     int tiles_x = (width + TILE - 1) / TILE;
     int64_t npix = (int64_t)width * height;
-    double cmax = max_rgb(n, rgb);
+    (void)n;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -460,7 +505,7 @@ void oracle_render(int width, int height, int row0, int row1, const uint32_t *ra
             int tile = (py / TILE) * tiles_x + px / TILE;
             uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
             pixel_t p = composite_pixel((double)px, (double)py, vals + s, (int64_t)e - (int64_t)s, xy, conic,
-                                        opacity, rgb, depth, bg, tau_alpha, tau_T, pos_eps, cmax);
+                                        opacity, rgb, depth, bg, tau_alpha, tau_T, pos_eps);
             store_pixel(&p, (int64_t)py * width + px, npix, out_color, invdepth, final_T, n_contrib, n_eval,
                         near_count, flip_impact);
         }
@@ -486,7 +531,6 @@ void oracle_render_bruteforce(int width, int height, int64_t n, const int32_t *r
                               double *out_color, double *invdepth, double *final_T, int32_t *n_contrib,
                               int32_t *n_eval, int32_t *near_count, double *flip_impact) {
     int64_t npix = (int64_t)width * height;
-    double cmax = max_rgb(n, rgb);
     uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     g_bf_depth = depth32;
     for (int py = 0; py < height; ++py)
@@ -503,7 +547,7 @@ void oracle_render_bruteforce(int width, int height, int64_t n, const int32_t *r
             }
             qsort(ids, (size_t)len, sizeof(uint32_t), bf_cmp);
             pixel_t p = composite_pixel((double)px, (double)py, ids, len, xy, conic, opacity, rgb, depth, bg, 0.0,
-                                        0.0, 0.0, cmax);
+                                        0.0, 0.0);
             store_pixel(&p, (int64_t)py * width + px, npix, out_color, invdepth, final_T, n_contrib, n_eval,
                         near_count, flip_impact);
         }

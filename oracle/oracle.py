@@ -178,9 +178,11 @@ def render(pre: dict, srt: dict, cam, bg=(0.0, 0.0, 0.0), tau_alpha: float = 0.0
            rows: tuple | None = None, threads: int = 0, pos_eps: float = 0.0) -> dict:
     """Tiled front-to-back compositing of every pixel in ``rows`` (default:
     all).  ``tau_alpha`` / ``tau_T`` set the log-space margin under which a
-    threshold decision counts as near (see ``near`` / ``flip_impact``);
-    ``pos_eps`` widens it by the effect of that relative rounding of each
-    splat's pixel coordinates."""
+    threshold decision counts as near; ``pos_eps`` widens it by the effect of
+    that relative rounding of each splat's pixel coordinates.  ``near``
+    counts a pixel's near decisions; ``flip_impact`` is the largest change of
+    a colour channel when one of them is taken the other way and the rest of
+    the list is walked again."""
     lib = _load()
     w, h = cam.width, cam.height
     r0, r1 = (0, h) if rows is None else rows

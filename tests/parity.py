@@ -7,9 +7,12 @@ IMAGE_ATOL = 2e-4
 TAU_ALPHA, TAU_T
     Log-space margins under which an alpha-threshold or transmittance-stop
     decision counts as "near": the FP32 path may take it the other way.
-    A pixel is excluded from the 2e-4 check only if such a near decision
-    could move it by more than IMAGE_ATOL / 2 (the oracle's flip_impact), and
-    excluded from the exact n_contrib check if it has any near decision.
+    A pixel is excluded from the 2e-4 check only if taking such a near
+    decision the other way moves it by more than IMAGE_ATOL / 2 (the oracle's
+    flip_impact: the pixel walked again with that one decision flipped, every
+    later decision re-evaluated, so a flip that moves a later stop counts in
+    full), and excluded from the exact n_contrib check if it has any near
+    decision.
     The FP32 error of the exponent from its own arithmetic is about 1e-6
     (ex2.approx relative error 2^-22, conic rounding); TAU_ALPHA = 1e-4
     leaves a factor of ~100.  Transmittance accumulates one rounding per

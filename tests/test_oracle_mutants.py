@@ -24,7 +24,7 @@ MUTANTS = {
     "jacobian_sign": ("-cam.fx * txc", "cam.fx * txc"),
     "colour_offset": ("fmax(acc + 0.5, 0.0)", "fmax(acc, 0.0)"),
     "sh_index": ("Y[l * l + l + mm]", "Y[l * l + l - mm]"),
-    "stop_not_permanent": ("if (Tn < T_MIN) break;", "if (Tn < T_MIN) continue;"),
+    "stop_not_permanent": ("if (stop) break;", "if (stop) continue;"),
     "invdepth_weight_without_T": ("D += alpha * T / depth[g];", "D += alpha / depth[g];"),
     "invdepth_depth_not_inverted": ("D += alpha * T / depth[g];", "D += alpha * T * depth[g];"),
     "n_contrib_blended_only": ("last = contrib;", "last = contrib - (contrib > 1);"),
@@ -47,16 +47,35 @@ MUTANTS = {
     "scale_not_squared": ("acc += R[i][k] * s[k] * s[k] * R[j][k];", "acc += R[i][k] * s[k] * R[j][k];"),
     "tile_id_transposed": ("(uint64_t)y * (uint64_t)tiles_x + (uint64_t)x", "(uint64_t)x * (uint64_t)tiles_x + (uint64_t)y"),
     "pixel_centre_offset": ("composite_pixel((double)px, (double)py, vals", "composite_pixel((double)px + 0.5, (double)py + 0.5, vals"),
+    # near-decision bookkeeping (which pixels a parity test may excuse)
+    "near_pos_err_dropped": ("double pos_err = pos_eps * (", "double pos_err = 0.0 * pos_eps * ("),
+    "near_pos_err_no_offset": ("(fabs(xy[2 * g]) + 1.0)", "fabs(xy[2 * g])"),
+    "alpha_margin_uses_tau_T": ("< tau_alpha + pos_err)", "< tau_T + pos_err)"),
+    "stop_margin_uses_tau_alpha": ("< tau_T + pos_err * alpha", "< tau_alpha + pos_err * alpha"),
+    "stop_margin_without_alpha_factor": ("pos_err * alpha / (1.0 - alpha))", "pos_err)"),
+    "flip_of_stop_ignored": ("if (flip == 2 * i + DECIDE_STOP) stop = !stop;", ""),
+    "flip_rewalk_never_stops": ("int stop = Tn < T_MIN;", "int stop = Tn < T_MIN && flip < 0;"),
+    "flip_impact_first_near_only": ("for (int64_t k = 0; k < near.n; ++k) {",
+                                    "for (int64_t k = 0; k < (near.n > 0 ? 1 : 0); ++k) {"),
+    "flip_impact_first_channel_only": ("for (int ch = 0; ch < 3; ++ch) impact = fmax(",
+                                       "for (int ch = 0; ch < 1; ++ch) impact = fmax("),
+    "edge_dist_no_clamp": ("if (k < 1.0 || k > (double)hi) return 1e30;", "(void)hi;"),
+    "edge_dist_drops_an_edge": ("e = fmin(e, rect_edge_dist(py - r, TILE, cam.tiles_y));", ""),
+    "rad_dist_of_lambda": ("rad_dist[g] = dist_to_int(rr);", "rad_dist[g] = dist_to_int(sqrt(fmax(lam1, lam2)));"),
 }
 
 
 def _pin_functions():
+    import test_oracle_exclusion as exclusion
     import test_oracle_pins as pins
     out = []
-    for name, fn in inspect.getmembers(pins, inspect.isfunction):
-        if not name.startswith("test_") or name == "test_unrestricted_bruteforce_difference_reported":
-            continue
-        out.append((name, fn))
+    for mod in (pins, exclusion):
+        for name, fn in inspect.getmembers(mod, inspect.isfunction):
+            if not name.startswith("test_") or name == "test_unrestricted_bruteforce_difference_reported":
+                continue
+            if fn.__module__ != mod.__name__:
+                continue  # imported helpers
+            out.append((f"{mod.__name__}.{name}", fn))
     return out
 
 

@@ -268,13 +268,16 @@ int gs_render_ex(const gs_splat *splats, const uint32_t *vals, const uint32_t *r
  * counterpart; this is a deployment convenience.
  *
  * Same arguments, results and errors as gs_sort minus the workspace.  The
- * scratch is a fixed 38 MiB array inside the library, which every GPU that
- * loads the library holds until the process exits; it bounds the sizes:
+ * scratch is a fixed 42 MiB array inside the library (the workspace gs_sort
+ * needs at the largest accepted n and m_cap, for any tile grid), which every
+ * GPU that loads the library holds until the process exits; it bounds the
+ * sizes:
  * n <= GS_SORT_STATIC_MAX_GAUSSIANS and m_cap <= GS_SORT_STATIC_MAX_INSTANCES,
  * else GS_ERR_TOO_LARGE (checked before any GPU work).  The call allocates
  * nothing.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current) and caches it:
- * make that first call before any stream capture.  All calls share the
+ * make that first call before any stream capture (a lookup that fails is
+ * not cached, so a later call outside capture retries it).  All calls share the
  * array; each call clears the counters that must start at zero, but calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
  * it, so serialise them.  With m_out NULL an overflow cannot be read back
@@ -318,6 +321,20 @@ typedef struct gs_render_batch_desc {
  * The caller must keep jobs' buffers alive until the launch completes.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t grid, void *stream);
+
+/* Failure-detection check of the sort's bounded waits (the paper has no
+ * counterpart).  gs_sort's radix passes and scans learn earlier blocks'
+ * counts by decoupled look-back; a block whose predecessor never publishes
+ * (it stalled or died) must not spin forever.  This call runs one look-back
+ * walk of block 1 whose predecessor, block 0, never runs, with its wait
+ * bounded by limit_ns nanoseconds (1 .. 1e9; gs_sort itself uses 1 s),
+ * synchronises `stream`, and returns GS_ERR_TIMEOUT when the wait gave up
+ * as it must (GS_OK would mean it found a flag nobody wrote).  workspace:
+ * device, 256-byte aligned, >= gs_sort_workspace_bytes(1, 1, 1) bytes; its
+ * header then records the timeout exactly as a failed gs_sort would, so
+ * gs_sort_status on it returns GS_ERR_TIMEOUT too.  The context stays
+ * usable.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_check_wait_timeout(void *workspace, size_t workspace_bytes, uint64_t limit_ns, void *stream);
 
 /* Text for a GS_* code, or the CUDA error string of the last GS_ERR_CUDA. */
 const char *gs_strerror(int code);

@@ -99,6 +99,8 @@ def lib():
         L.gs_preprocess_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P,
                                              ctypes.POINTER(GsSceneGrads), P]
         L.gs_preprocess_backward.restype = ctypes.c_int
+        L.gs_check_wait_timeout.argtypes = [P, c_size_t, ctypes.c_uint64, P]
+        L.gs_check_wait_timeout.restype = ctypes.c_int
         L.gs_strerror.argtypes = [ctypes.c_int]
         L.gs_strerror.restype = ctypes.c_char_p
         L.gs_last_cuda_error.restype = ctypes.c_char_p
@@ -124,5 +126,5 @@ def exported_symbols():
     return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
             "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
             "gs_render_backward", "gs_render_backward_splats", "gs_preprocess_backward",
-            "gs_render_batch",
+            "gs_render_batch", "gs_check_wait_timeout",
             "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

@@ -38,6 +38,7 @@ cudaError_t launch_render_backward_splats(int64_t n, const CamParams &cam, const
                                           float *dsplat, cudaStream_t st);
 cudaError_t launch_preprocess_backward(const gs_scene &s, const CamParams &cam, const gs_splat *splats,
                                        const float *dsplat, const gs_scene_grads &g, cudaStream_t st);
+cudaError_t launch_lookback_probe(const SortWs &ws, uint64_t limit_ns, cudaStream_t st);
 cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
@@ -141,6 +142,21 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream) {
     *m_out = (int64_t)h.m_total;
     if (h.timeout) return GS_ERR_TIMEOUT;
     return h.overflow ? GS_ERR_CAPACITY : GS_OK;
+}
+
+int gs_check_wait_timeout(void *workspace, size_t workspace_bytes, uint64_t limit_ns, void *stream) {
+    gs::NvtxRange nvtx_range("gs_check_wait_timeout");
+    if (!workspace || !aligned(workspace, 256) || limit_ns == 0 || limit_ns > 1000000000ull) return GS_ERR_INVALID_ARG;
+    if (workspace_bytes < carve_sort_ws(nullptr, 1, 1, 1, nullptr)) return GS_ERR_INVALID_ARG;
+    SortWs ws;
+    carve_sort_ws(static_cast<char *>(workspace), 1, 1, 1, &ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_lookback_probe(ws, limit_ns, st);
+    SortHeader h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ws.hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return h.timeout ? GS_ERR_TIMEOUT : GS_OK;
 }
 
 static int render_common(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,

@@ -53,7 +53,8 @@ constexpr int kBins = 256;
 constexpr uint64_t kFlagAgg = 1ull << 62;        // block aggregate published
 constexpr uint64_t kFlagPre = 2ull << 62;        // inclusive prefix published
 constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // default bound on one wait
+constexpr uint32_t kWaitMaxPolls = 1u << 26;       // and on its polls (>= 2 s at >= 32 ns each)
 
 enum Counter { kCtrCompact = 0, kCtrDepth = 1, kCtrOffsets = 5, kCtrTiles = 6 };
 
@@ -76,16 +77,19 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Waits (bounded) until *p carries a flag.  On timeout -- or once any wait
 // of this call has timed out -- records it and returns an empty inclusive
 // prefix so the caller's walk ends: a fault costs at most ~1 s per kernel.
+// The bound is the header's wait_limit_ns (0: 1 s) of %globaltimer, and a
+// poll count that ends the wait even if the timer stood still.
 __device__ uint64_t wait_flag(const uint64_t *p, SortHeader *hdr) {
     uint64_t v = ld_relaxed(p);
     if (v >> 62) return v;
     volatile uint32_t *timeout = &hdr->timeout;
+    const uint64_t limit = hdr->wait_limit_ns ? hdr->wait_limit_ns : kWaitLimitNs;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         __nanosleep(32);
         v = ld_relaxed(p);
         if (v >> 62) return v;
-        if ((it & 63u) == 0u && (*timeout != 0u || global_ns() - t0 > kWaitLimitNs)) {
+        if ((it & 63u) == 0u && (*timeout != 0u || global_ns() - t0 > limit || it >= kWaitMaxPolls)) {
             atomicExch(&hdr->timeout, 1u);
             return kFlagPre;
         }
@@ -732,7 +736,27 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict_
     if (lane == 0) ranges[t] = s < e ? make_uint2(s, e) : make_uint2(0u, 0u);
 }
 
+// The failure-detection check: one look-back walk of block 1 whose only
+// predecessor (block 0) never publishes, as when a block stalls or dies.
+// The walk's bounded wait must give up after wait_limit_ns, record the
+// timeout in the header and end the walk.  One thread; the state words are
+// zeroed by the host first.
+__global__ void lookback_probe_kernel(uint64_t *state, SortHeader *hdr, uint64_t limit_ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    hdr->wait_limit_ns = limit_ns;
+    walk_back<kTileWin>(state, 1u, 1u, 1ull, hdr);
+}
+
 }  // namespace
+
+// Runs lookback_probe_kernel on a zeroed header and two state words of `ws`.
+cudaError_t launch_lookback_probe(const SortWs &ws, uint64_t limit_ns, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ws.hdr, 0, sizeof(SortHeader), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.scan_state[0], 0, 2 * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    lookback_probe_kernel<<<1, 32, 0, st>>>(ws.scan_state[0], ws.hdr, limit_ns);
+    return cudaGetLastError();
+}
 
 // Steps 1-3 (through M).
 cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,

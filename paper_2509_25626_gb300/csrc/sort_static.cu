@@ -8,10 +8,12 @@
 // a caller-provided workspace.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads
-// the library holds it (38 MiB) until the process exits.  Host code cannot
-// use the array's name as a device address, so the first call on each
-// device resolves the address with cudaGetSymbolAddress (with that device
-// current) and caches it; make that first call before any stream capture.
+// the library holds it (42 MiB: the workspace gs_sort needs at the largest
+// accepted n and m_cap, for any tile grid) until the process exits.  Host
+// code cannot use the array's name as a device address, so the first call
+// on each device resolves the address with cudaGetSymbolAddress (with that
+// device current) and caches it; make that first call before any stream
+// capture.  A failed lookup is not cached: the next call tries again.
 // All calls share the one array: the part that must start at zero (the
 // counters header) is cleared by every call, and calls whose work overlaps
 // on the GPU (concurrent streams, or several host threads) race on it.
@@ -30,17 +32,19 @@ void set_cuda_error(cudaError_t e);
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = (size_t)38 << 20;  // >= carve_sort_ws(max n, max m_cap)
+// The workspace at the largest accepted sizes; the tile grid only changes
+// how many tile passes are laid out, and 2^32 tiles takes the most.
+constexpr size_t kStaticBound =
+    sort_ws_offsets(GS_SORT_STATIC_MAX_GAUSSIANS, GS_SORT_STATIC_MAX_INSTANCES, 1ull << 32).total;
+constexpr size_t kStaticScratchBytes = (kStaticBound + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+static_assert(kStaticScratchBytes >= kStaticBound, "static scratch below the workspace bound");
+static_assert(kStaticScratchBytes == (size_t)42 << 20, "the 42 MiB stated in gs.h");
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_sort_scratch[kStaticScratchBytes];
 
-struct DeviceScratch {
-    std::once_flag once;
-    void *ptr = nullptr;
-    cudaError_t err = cudaSuccess;
-};
-DeviceScratch g_scratch[kMaxDevices];
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};  // device address per device, once looked up
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -69,20 +73,24 @@ extern "C" int gs_sort_static(const gs_splat *splats, int64_t n, const gs_camera
         return GS_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) return GS_ERR_INVALID_ARG;
-    DeviceScratch &slot = g_scratch[dev];
-    std::call_once(slot.once, [&slot] {
-        void *p = nullptr;
-        slot.err = cudaGetSymbolAddress(&p, g_sort_scratch);
-        slot.ptr = p;
-    });
-    if (slot.err != cudaSuccess || !slot.ptr) {
-        set_cuda_error(slot.err != cudaSuccess ? slot.err : cudaErrorInvalidSymbol);
-        return GS_ERR_CUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_ptr[dev]) {  // only a successful lookup is kept
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_sort_scratch);
+            if (e != cudaSuccess || !p) {
+                set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+                return GS_ERR_CUDA;
+            }
+            g_scratch_ptr[dev] = p;
+        }
+        scratch = g_scratch_ptr[dev];
     }
 
     cudaStream_t st = (cudaStream_t)stream;
     SortWs ws;
-    carve_sort_ws(static_cast<char *>(slot.ptr), n, m_cap, num_tiles, &ws);
+    carve_sort_ws(static_cast<char *>(scratch), n, m_cap, num_tiles, &ws);
     e = launch_sort_front(splats, n, ws, (uint64_t)m_cap, (int)tiles_x, (uint32_t)num_tiles, st);
     if (e == cudaSuccess && m_out) {
         SortHeader h;

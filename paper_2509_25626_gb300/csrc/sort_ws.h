@@ -19,7 +19,8 @@ struct SortHeader {
     uint32_t overflow;     // 1 if m_total > m_cap
     uint32_t timeout;      // 1 if a bounded look-back wait gave up (results invalid)
     uint32_t tile_ctr[10]; // dynamic block-id counters, one per look-back kernel
-    uint32_t reserved[48];
+    uint64_t wait_limit_ns;  // bound on one look-back wait; 0 = the default (1 s)
+    uint32_t reserved[46];
 };
 static_assert(sizeof(SortHeader) == 256, "header is 256 bytes");
 
@@ -40,17 +41,17 @@ struct SortWs {
     uint32_t *tkey, *tval;              // tile sort buffer, [m_cap] each
 };
 
-inline uint64_t sort_blocks_for(uint64_t count) { return (count + kSortTileItems - 1) / kSortTileItems; }
-inline uint64_t depth_blocks_for(uint64_t count) { return (count + kDepthItems - 1) / kDepthItems; }
-inline uint64_t tile_pass_blocks_for(uint64_t count) { return (count + kTilePassItems - 1) / kTilePassItems; }
+constexpr uint64_t sort_blocks_for(uint64_t count) { return (count + kSortTileItems - 1) / kSortTileItems; }
+constexpr uint64_t depth_blocks_for(uint64_t count) { return (count + kDepthItems - 1) / kDepthItems; }
+constexpr uint64_t tile_pass_blocks_for(uint64_t count) { return (count + kTilePassItems - 1) / kTilePassItems; }
 
-inline int tile_bits_of(uint64_t num_tiles) {
+constexpr int tile_bits_of(uint64_t num_tiles) {
     int b = 0;
     while (b < 32 && (1ull << b) < num_tiles) ++b;
     return b;
 }
 
-inline int tile_passes_of(uint64_t num_tiles) {
+constexpr int tile_passes_of(uint64_t num_tiles) {
     const int p = (tile_bits_of(num_tiles) + 7) / 8;
     return p < 1 ? 1 : p;
 }
@@ -83,45 +84,83 @@ inline TileKeyLayout tile_key_layout(uint32_t tiles_x, uint32_t tiles_y) {
 
 // Tile passes the workspace is sized for: the byte-aligned key needs at most
 // one pass more than the packed tile id.
-inline int tile_passes_bound(uint64_t num_tiles) {
+constexpr int tile_passes_bound(uint64_t num_tiles) {
     const int p = tile_passes_of(num_tiles) + 1;
     return p < kMaxTilePasses ? p : kMaxTilePasses;
 }
 
-// Carves `base` (may be null to only measure) and returns the bytes needed.
-inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, uint64_t num_tiles, SortWs *ws) {
+// Byte offsets of the workspace regions (256-byte aligned, in this order);
+// a constant expression, so that a fixed-size workspace can be checked
+// against it at compile time.  kNone marks a tile pass the grid never runs.
+struct SortWsOffsets {
+    static constexpr size_t kNone = ~(size_t)0;
+    size_t hdr = 0, scan_state[2] = {}, depth_state[4] = {}, tile_state[kMaxTilePasses] = {}, hist_depth = 0,
+           hist_tile = 0, zero_bytes = 0, dkey[2] = {}, dval[2] = {}, depthv = 0, rectv = 0, srect = 0, offs = 0,
+           dup_start = 0, tkey = 0, tval = 0, total = 0;
+};
+
+constexpr SortWsOffsets sort_ws_offsets(int64_t n, int64_t m_cap, uint64_t num_tiles) {
+    SortWsOffsets o;
     size_t off = 0;
-    auto take = [&](size_t bytes) -> char * {
-        char *p = base ? base + off : nullptr;
+    auto take = [&off](size_t bytes) {
+        const size_t at = off;
         off += (bytes + 255) & ~(size_t)255;
-        return p;
+        return at;
     };
     const uint64_t nn = (uint64_t)(n > 0 ? n : 0), mc = (uint64_t)(m_cap > 0 ? m_cap : 0);
     const uint64_t bn = sort_blocks_for(nn) + 1, bm = sort_blocks_for(mc) + 1, bd = depth_blocks_for(nn) + 1;
     const uint64_t bt = tile_pass_blocks_for(mc) + 1;
     const int passes = tile_passes_bound(num_tiles);
-    SortWs w{};
-    w.hdr = reinterpret_cast<SortHeader *>(take(sizeof(SortHeader)));
-    for (int i = 0; i < 2; ++i) w.scan_state[i] = reinterpret_cast<uint64_t *>(take(8 * bn));
-    for (int i = 0; i < 4; ++i) w.depth_state[i] = reinterpret_cast<uint64_t *>(take(8 * 256 * bd));
+    o.hdr = take(256);  // sizeof(SortHeader)
+    for (int i = 0; i < 2; ++i) o.scan_state[i] = take(8 * bn);
+    for (int i = 0; i < 4; ++i) o.depth_state[i] = take(8 * 256 * bd);
     for (int i = 0; i < kMaxTilePasses; ++i)  // pass 0 (fused with duplication) uses 4096-element blocks
-        w.tile_state[i] = reinterpret_cast<uint64_t *>(i < passes ? take(8 * 256 * (i == 0 ? bm : bt)) : nullptr);
-    w.hist_depth = reinterpret_cast<uint32_t *>(take(4 * 4 * 256));
-    w.hist_tile = reinterpret_cast<uint32_t *>(take(4 * kMaxTilePasses * 257));
-    w.zero_bytes = off;
+        o.tile_state[i] = i < passes ? take(8 * 256 * (i == 0 ? bm : bt)) : SortWsOffsets::kNone;
+    o.hist_depth = take(4 * 4 * 256);
+    o.hist_tile = take(4 * kMaxTilePasses * 257);
+    o.zero_bytes = off;
     for (int i = 0; i < 2; ++i) {
-        w.dkey[i] = reinterpret_cast<uint32_t *>(take(4 * nn));
-        w.dval[i] = reinterpret_cast<uint32_t *>(take(4 * nn));
+        o.dkey[i] = take(4 * nn);
+        o.dval[i] = take(4 * nn);
     }
-    w.depthv = reinterpret_cast<uint32_t *>(take(4 * nn));
-    w.rectv = reinterpret_cast<uint2 *>(take(8 * nn));
-    w.srect = reinterpret_cast<uint2 *>(take(8 * nn));
-    w.offs = reinterpret_cast<uint32_t *>(take(4 * nn));
-    w.dup_start = reinterpret_cast<uint32_t *>(take(4 * (sort_blocks_for(mc) + 2)));
-    w.tkey = reinterpret_cast<uint32_t *>(take(4 * mc));
-    w.tval = reinterpret_cast<uint32_t *>(take(4 * mc));
-    if (ws) *ws = w;
-    return off;
+    o.depthv = take(4 * nn);
+    o.rectv = take(8 * nn);
+    o.srect = take(8 * nn);
+    o.offs = take(4 * nn);
+    o.dup_start = take(4 * (sort_blocks_for(mc) + 2));
+    o.tkey = take(4 * mc);
+    o.tval = take(4 * mc);
+    o.total = off;
+    return o;
+}
+
+// Carves `base` (may be null to only measure) and returns the bytes needed.
+inline size_t carve_sort_ws(char *base, int64_t n, int64_t m_cap, uint64_t num_tiles, SortWs *ws) {
+    const SortWsOffsets o = sort_ws_offsets(n, m_cap, num_tiles);
+    if (ws) {
+        auto at = [base](size_t off) -> char * { return base && off != SortWsOffsets::kNone ? base + off : nullptr; };
+        SortWs w{};
+        w.hdr = reinterpret_cast<SortHeader *>(at(o.hdr));
+        for (int i = 0; i < 2; ++i) w.scan_state[i] = reinterpret_cast<uint64_t *>(at(o.scan_state[i]));
+        for (int i = 0; i < 4; ++i) w.depth_state[i] = reinterpret_cast<uint64_t *>(at(o.depth_state[i]));
+        for (int i = 0; i < kMaxTilePasses; ++i) w.tile_state[i] = reinterpret_cast<uint64_t *>(at(o.tile_state[i]));
+        w.hist_depth = reinterpret_cast<uint32_t *>(at(o.hist_depth));
+        w.hist_tile = reinterpret_cast<uint32_t *>(at(o.hist_tile));
+        w.zero_bytes = o.zero_bytes;
+        for (int i = 0; i < 2; ++i) {
+            w.dkey[i] = reinterpret_cast<uint32_t *>(at(o.dkey[i]));
+            w.dval[i] = reinterpret_cast<uint32_t *>(at(o.dval[i]));
+        }
+        w.depthv = reinterpret_cast<uint32_t *>(at(o.depthv));
+        w.rectv = reinterpret_cast<uint2 *>(at(o.rectv));
+        w.srect = reinterpret_cast<uint2 *>(at(o.srect));
+        w.offs = reinterpret_cast<uint32_t *>(at(o.offs));
+        w.dup_start = reinterpret_cast<uint32_t *>(at(o.dup_start));
+        w.tkey = reinterpret_cast<uint32_t *>(at(o.tkey));
+        w.tval = reinterpret_cast<uint32_t *>(at(o.tval));
+        *ws = w;
+    }
+    return o.total;
 }
 
 }  // namespace gs

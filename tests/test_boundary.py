@@ -102,6 +102,13 @@ def test_invalid_arguments_rejected_on_host(L):
     assert lib.gs_render(P(256), P(256), P(256), ctypes.byref(cam), bg_nan, P(256), P(256), P(256), None) == \
         L.GS_ERR_INVALID_ARG
     assert lib.gs_sort_status(None, ctypes.byref(m), None) == L.GS_ERR_INVALID_ARG
+    # gs_check_wait_timeout: null, misaligned or small workspace, limit outside 1 .. 1e9 ns
+    ws_bytes = lib.gs_sort_workspace_bytes(1, 1, 1)
+    assert lib.gs_check_wait_timeout(None, ws_bytes, 1000, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_check_wait_timeout(P(256 + 16), ws_bytes, 1000, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_check_wait_timeout(P(256), ws_bytes - 1, 1000, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_check_wait_timeout(P(256), ws_bytes, 0, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_check_wait_timeout(P(256), ws_bytes, 2_000_000_000, None) == L.GS_ERR_INVALID_ARG
 
 
 def test_workspace_size_monotone(L):
@@ -111,6 +118,17 @@ def test_workspace_size_monotone(L):
     c = lib.gs_sort_workspace_bytes(2000, 20_000, 100)
     assert 0 < a < b < c
     assert lib.gs_sort_workspace_bytes(0, 0, 1) > 0
+
+
+def test_static_sort_scratch_covers_its_limits(L):
+    """gs_sort_static's fixed 42 MiB array holds gs_sort's workspace at the
+    largest n and m_cap it accepts, for every tile grid (the grid only sets
+    how many tile passes are laid out)."""
+    lib = L.lib()
+    scratch = 42 << 20
+    for tiles in (1, 200, 6630, 32400, 65536, 1 << 20, (1 << 31) - 1):
+        need = lib.gs_sort_workspace_bytes(L.SORT_STATIC_MAX_GAUSSIANS, L.SORT_STATIC_MAX_INSTANCES, tiles)
+        assert 0 < need <= scratch, (tiles, need)
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

@@ -14,7 +14,7 @@ import paper_2509_25626_gb300 as gs
 from paper_2509_25626_gb300 import SPLAT_DTYPE, SceneTensors
 from parity import records_from_oracle
 from synth import clustered_scene, orbit_camera, subset_scene
-from test_oracle_grad import grad_scene, loss_and_structure
+from test_oracle_grad import central_difference, clamp_scene, grad_scene, loss_and_structure
 
 pytestmark = pytest.mark.gpu
 
@@ -23,16 +23,19 @@ NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
 BG = (0.1, 0.2, 0.3)
 
 
-def gpu_grads(sc, cam, dL, bg=BG):
+def gpu_grads(sc, cam, dL, bg=BG, m_cap=None, forward=False):
     st = SceneTensors.from_scene(sc, DEV)
     sp = gs.preprocess(st, cam)
-    keys, vals, ranges, m, _ = gs.sort(sp, sc.n, cam, max(1024, 64 * sc.n))
+    keys, vals, ranges, m, _ = gs.sort(sp, sc.n, cam, m_cap or max(1024, 64 * sc.n))
     img, T, nc = gs.render(sp, vals, ranges, cam, bg)
     dLt = torch.from_numpy(np.ascontiguousarray(dL, np.float32)).to(DEV)
     grads, dsplat = gs.render_backward(st, cam, sp, vals, ranges, T, nc, dLt, bg)
     torch.cuda.synchronize()
     recs = sp.cpu().numpy().view(SPLAT_DTYPE).reshape(-1)[: sc.n]
-    return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}, img.cpu().numpy(), recs
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    if forward:
+        return g, (img.cpu().numpy(), T.cpu().numpy(), nc.cpu().numpy()), recs
+    return g, img.cpu().numpy(), recs
 
 
 def no_rect_flips(recs, pre):
@@ -45,9 +48,11 @@ def rel_err(a, b):
 
 
 def backward_scenes():
-    out = [("grad512_s3",) + grad_scene(seed=3), ("grad512_s8",) + grad_scene(seed=8)]
+    out = [("grad512_s3",) + grad_scene(seed=3), ("grad512_s8",) + grad_scene(seed=8),
+           ("clamp512_s4",) + clamp_scene(seed=4), ("clamp512_s9",) + clamp_scene(seed=9)]
     clu = clustered_scene(20000, seed=6)
-    # keep the clustered scene away from the clamps, as the FD scenes are
+    out.append(("clustered20k_orbit5_raw", clu, orbit_camera(5, 20, 4.0, 160, 120)))  # the recipe's own logits
+    clu = clustered_scene(20000, seed=6)
     clu.opacity_logits[:] = np.clip(clu.opacity_logits, -3.0, 3.0)
     for k in (2, 11):
         out.append((f"clustered20k_orbit{k}", clu, orbit_camera(k, 20, 4.0, 160, 120)))
@@ -57,11 +62,15 @@ def backward_scenes():
 @pytest.mark.parametrize("case", [c[0] for c in backward_scenes()])
 def test_backward_matches_oracle_gradient(oracle, case):
     from oracle import grad as G
+    from parity import POS_EPS_E2E, TAU_ALPHA, TAU_T
     name, sc, cam = next(c for c in backward_scenes() if c[0] == case)
     dL = np.random.default_rng(1).normal(size=(3, cam.height, cam.width))
-    g_gpu, img, recs = gpu_grads(sc, cam, dL)
-    pre = oracle.preprocess(sc, cam)
+    pre, srt, ora = oracle.frame(sc, cam, BG, TAU_ALPHA, TAU_T, pos_eps=POS_EPS_E2E)
+    dL[:, ora["near"] > 0] = 0.0  # pixels whose FP32 walk may legitimately take another piece
+    g_gpu, (img, T, nc), recs = gpu_grads(sc, cam, dL, forward=True)
     assert no_rect_flips(recs, pre), "an FP32 rectangle flip changes the lists; pick another seed"
+    exact = ora["near"] == 0
+    assert np.array_equal(nc[exact], ora["n_contrib"][exact]), "the forward's decisions differ"
     img_ref, _, g_ref = G.forward_and_grad(sc, cam, dL, BG)
     report = {}
     for k in NAMES:
@@ -71,10 +80,15 @@ def test_backward_matches_oracle_gradient(oracle, case):
     print(name, {k: f"{v:.2e}" for k, v in report.items()})
 
 
-def test_backward_matches_central_differences(oracle):
-    """Direct check against FP64 central differences of the C oracle."""
-    sc, cam = grad_scene(seed=5)
+@pytest.mark.parametrize("scene", ["grad5", "clamp6"])
+def test_backward_matches_central_differences(oracle, scene):
+    """Direct check against FP64 central differences of the C oracle, also
+    with the 0.99 clamp active."""
+    from parity import POS_EPS_E2E, TAU_ALPHA, TAU_T
+    sc, cam = grad_scene(seed=5) if scene == "grad5" else clamp_scene(seed=6)
     dL = np.random.default_rng(5).normal(size=(3, cam.height, cam.width))
+    ora = oracle.frame(sc, cam, BG, TAU_ALPHA, TAU_T, pos_eps=POS_EPS_E2E)[2]
+    dL[:, ora["near"] > 0] = 0.0  # pixels whose FP32 walk may legitimately take another piece
     g_gpu, _, recs = gpu_grads(sc, cam, dL)
     pre = oracle.preprocess(sc, cam)
     assert no_rect_flips(recs, pre)
@@ -87,19 +101,11 @@ def test_backward_matches_central_differences(oracle):
         while len(fd) < 30 and tried < 300:
             tried += 1
             g = int(rng.choice(vis))
-            flat = arr.reshape(arr.shape[0], -1)
-            k = int(rng.integers(flat.shape[1]))
-            orig = np.float32(flat[g, k])
-            h = np.float32(max(1e-5 * abs(float(orig)), 1e-6))
-            plus, minus = np.float32(orig + h), np.float32(orig - h)
-            flat[g, k] = plus
-            lp, sp = loss_and_structure(oracle, sc, cam, dL, BG)
-            flat[g, k] = minus
-            lm, sm = loss_and_structure(oracle, sc, cam, dL, BG)
-            flat[g, k] = orig
-            if sp != base or sm != base:
+            k = int(rng.integers(arr.reshape(arr.shape[0], -1).shape[1]))
+            d = central_difference(oracle, sc, cam, dL, BG, arr, g, k, base)
+            if d is None:
                 continue
-            fd.append((lp - lm) / (float(plus) - float(minus)))
+            fd.append(d)
             gg.append(g_gpu[name].reshape(g_gpu[name].shape[0], -1)[g, k])
         fd, gg = np.array(fd), np.array(gg)
         assert len(fd) >= 15
@@ -156,3 +162,49 @@ def test_split_backward_equals_combined():
     g2 = gs.preprocess_backward(st, cam, sp, dsplat.contiguous())
     for k in NAMES:
         assert torch.equal(g2[k], grads[k]), k
+
+
+@pytest.mark.parametrize("tile_rows", [(5, 7), (25, 27)])
+def test_backward_full_size_band(oracle, tile_rows):
+    """The backward workload at full size -- 1M Gaussians of the clustered
+    recipe at 1237x822, pose 0, in the launch configuration the benchmark
+    times -- with dL/dpixel ~ N(0, 1) on two tile rows and zero elsewhere:
+    every gradient tensor within 1e-3 (relative norm) of the FP64 gradient
+    oracle, which renders and differentiates only those rows (rectangles
+    clipped to them, which keeps their lists and order).  The pixels of
+    those rows walk lists of ~400-600 splats, so the transmittance recovered
+    back to front through T_after / (1 - alpha) is exercised over the
+    benchmark's list depths.  Pixels with a near decision get dL = 0."""
+    from oracle import grad as G
+    from parity import POS_EPS_E2E, TAU_ALPHA, TAU_T, rect_of
+    sc = clustered_scene(1_000_000, seed=3)
+    cam = orbit_camera(0, 20, 4.0, 1237, 822)
+    ty0, ty1 = tile_rows
+    r0, r1 = 16 * ty0, 16 * ty1
+    pre = oracle.preprocess(sc, cam)
+    clip = G.clip_to_tile_rows(pre, ty0, ty1)
+    srt = oracle.duplicate_sort(clip, cam)
+    ora = oracle.render(clip, srt, cam, BG, TAU_ALPHA, TAU_T, rows=(r0, r1), pos_eps=POS_EPS_E2E)
+    dL = np.zeros((3, cam.height, cam.width))
+    dL[:, r0:r1] = np.random.default_rng(ty0).normal(size=(3, r1 - r0, cam.width))
+    near = ora["near"][r0:r1] > 0
+    dL[:, r0:r1][:, near] = 0.0
+    g_gpu, (img, T, nc), recs = gpu_grads(sc, cam, dL, m_cap=8 * sc.n, forward=True)
+    # the band's lists are the oracle's: no rectangle of a Gaussian reaching
+    # these rows differs
+    rg = rect_of(recs)
+    band_g = ((pre["tiles"] > 0) & (pre["rect"][:, 1] < ty1) & (pre["rect"][:, 3] > ty0)) | \
+             ((recs["tiles_touched"] > 0) & (rg[:, 1] < ty1) & (rg[:, 3] > ty0))
+    diff = np.any(rg != pre["rect"], axis=1) | (recs["tiles_touched"].astype(np.int64) != pre["tiles"])
+    assert not np.any(diff & band_g), "a rectangle reaching the band flipped; pick other rows"
+    exact = ora["near"][r0:r1] == 0
+    assert np.array_equal(nc[r0:r1][exact], ora["n_contrib"][r0:r1][exact]), "the forward's decisions differ"
+    lens = srt["ranges"][:, 1].astype(np.int64) - srt["ranges"][:, 0]
+    _, _, g_ref = G.forward_and_grad(sc, cam, dL, BG, tile_rows=(ty0, ty1))
+    report = {}
+    for k in NAMES:
+        e = rel_err(g_gpu[k], g_ref[k])
+        report[k] = e
+        assert e <= 1e-3, f"band {tile_rows} {k}: relative error {e:.3e}"
+    print("bwd full size band", tile_rows, "mean list", float(lens[lens > 0].mean()), "n_contrib mean",
+          float(nc[r0:r1].mean()), "near px", int(near.sum()), {k: f"{v:.2e}" for k, v in report.items()})

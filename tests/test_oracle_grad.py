@@ -29,6 +29,37 @@ def grad_scene(n=512, seed=3, w=64, h=64):
     return sc, cam
 
 
+def clamp_scene(n=512, seed=4, w=64, h=64):
+    """The same kind of sub-scene with the 0.99 clamp active: opacity logits
+    N(4, 3) clipped to [-8, 8] (40 % of the Gaussians above opacity 0.99,
+    sigmoid(4.6)) and wider splats, so that blends with alpha clamped at 0.99
+    (zero gradient through the clamped alpha) and many with alpha near it
+    occur, and recovering the transmittance in front of such a splat divides
+    by 1 - alpha ~ 0.01."""
+    sc, cam = tiny_scene(n, seed, w, h, log_scale=(-2.0, 0.4))
+    rng = np.random.default_rng(seed + 200)
+    sc.opacity_logits[:] = np.clip(rng.normal(4.0, 3.0, size=n), -8.0, 8.0).astype(np.float32)
+    sc.sh[:, 0, :] = np.abs(rng.normal(0.0, 0.5, size=(n, 3))).astype(np.float32) + 0.3
+    return sc, cam
+
+
+def blend_alphas(oracle, sc, cam):
+    """The raw alpha o exp(power) of every blended (pixel, Gaussian) pair of
+    the oracle's forward (the test's own walk over the oracle's lists)."""
+    pre, srt, img = oracle.frame(sc, cam)
+    out = []
+    for py in range(cam.height):
+        for px in range(cam.width):
+            t = (py // 16) * cam.tiles_x + px // 16
+            s = srt["ranges"][t, 0]
+            for j in range(int(img["n_contrib"][py, px])):
+                g = srt["vals"][s + j]
+                dx, dy = pre["xy"][g, 0] - px, pre["xy"][g, 1] - py
+                a, b, c = pre["conic"][g]
+                out.append(pre["opacity"][g] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy))
+    return np.array(out)
+
+
 def loss_and_structure(oracle, sc, cam, dL, bg):
     pre, srt, img = oracle.frame(sc, cam, bg=bg)
     loss = float((img["color"] * dL).sum())
@@ -36,9 +67,37 @@ def loss_and_structure(oracle, sc, cam, dL, bg):
     return loss, struct
 
 
-def test_grad_forward_matches_c_oracle(oracle):
+def central_difference(oracle, sc, cam, dL, bg, arr, g, k, base_struct):
+    """FP64 central difference of the C oracle's loss sum(dL * image) in the
+    float32 parameter arr[g, k] (flattened per Gaussian), or None where the
+    loss is not smooth across the stencil: a discrete decision (rectangle,
+    skip, stop) changes, or the differences at steps h and h / 2 disagree,
+    which a kink that the structure does not show (a raw alpha crossing the
+    0.99 clamp, the frustum clamp of the Jacobian) inside the stencil
+    causes.  On a smooth piece the two agree to O(h^2)."""
+    flat = arr.reshape(arr.shape[0], -1)
+    orig = np.float32(flat[g, k])
+    out = []
+    for rel in (1e-5, 5e-6):
+        h = np.float32(max(rel * abs(float(orig)), 1e-6 * rel / 1e-5))
+        plus, minus = np.float32(orig + h), np.float32(orig - h)
+        flat[g, k] = plus
+        lp, sp = loss_and_structure(oracle, sc, cam, dL, bg)
+        flat[g, k] = minus
+        lm, sm = loss_and_structure(oracle, sc, cam, dL, bg)
+        flat[g, k] = orig
+        if sp != base_struct or sm != base_struct:
+            return None
+        out.append((lp - lm) / (float(plus) - float(minus)))
+    if abs(out[0] - out[1]) > 1e-6 * abs(out[1]) + 1e-12:
+        return None
+    return out[1]
+
+
+@pytest.mark.parametrize("scene", ["grad3", "clamp4"])
+def test_grad_forward_matches_c_oracle(oracle, scene):
     from oracle import grad as G
-    sc, cam = grad_scene()
+    sc, cam = grad_scene() if scene == "grad3" else clamp_scene()
     bg = (0.1, 0.2, 0.3)
     dL = np.random.default_rng(0).normal(size=(3, cam.height, cam.width))
     img, T, _ = G.forward_and_grad(sc, cam, dL, bg)
@@ -47,10 +106,21 @@ def test_grad_forward_matches_c_oracle(oracle):
     np.testing.assert_allclose(T, ora["final_T"], atol=1e-12)
 
 
-@pytest.mark.parametrize("seed", [3, 8])
+def test_clamp_scene_exercises_the_clamp(oracle):
+    sc, cam = clamp_scene()
+    raw = blend_alphas(oracle, sc, cam)
+    assert (raw > 0.99).sum() >= 20      # clamped blends
+    assert (raw > 0.9).sum() >= 1000     # 1 - alpha near 0.01 .. 0.1 in the T recovery
+
+
+@pytest.mark.parametrize("seed", [3, 8, "clamp4"])
 def test_grad_matches_central_differences(oracle, seed):
     from oracle import grad as G
-    sc, cam = grad_scene(seed=seed)
+    if seed == "clamp4":
+        sc, cam = clamp_scene(seed=4)
+        seed = 4
+    else:
+        sc, cam = grad_scene(seed=seed)
     bg = (0.1, 0.2, 0.3)
     rng = np.random.default_rng(seed)
     dL = rng.normal(size=(3, cam.height, cam.width))
@@ -69,17 +139,10 @@ def test_grad_matches_central_differences(oracle, seed):
             k = int(rng.integers(flat.shape[1]))
             if name == "sh" and k // 3 >= (sc.sh_degree + 1) ** 2:
                 continue
-            orig = np.float32(flat[g, k])
-            h = np.float32(max(1e-5 * abs(float(orig)), 1e-6))
-            plus, minus = np.float32(orig + h), np.float32(orig - h)
-            flat[g, k] = plus
-            lp, sp = loss_and_structure(oracle, sc, cam, dL, bg)
-            flat[g, k] = minus
-            lm, sm = loss_and_structure(oracle, sc, cam, dL, bg)
-            flat[g, k] = orig
-            if sp != base_struct or sm != base_struct:
-                continue  # a discrete decision flipped inside the stencil
-            fd_vals.append((lp - lm) / (float(plus) - float(minus)))
+            fd = central_difference(oracle, sc, cam, dL, bg, arr, g, k, base_struct)
+            if fd is None:
+                continue  # the loss is not smooth across the stencil
+            fd_vals.append(fd)
             ag_vals.append(ag[name].reshape(ag[name].shape[0], -1)[g, k])
         fd_vals, ag_vals = np.array(fd_vals), np.array(ag_vals)
         assert len(fd_vals) >= 20, f"{name}: too few clean samples"
@@ -87,3 +150,24 @@ def test_grad_matches_central_differences(oracle, seed):
         err = np.abs(fd_vals - ag_vals)
         assert np.all(err <= 1e-4 * np.abs(ag_vals) + 1e-5 * scale), \
             f"{name}: max err {err.max():.3e} (scale {scale:.3e})"
+
+
+def test_tile_row_band_equals_full_gradient(oracle):
+    """forward_and_grad restricted to tile rows [ty0, ty1) (rectangles clipped
+    to them) gives the full computation's gradient when dL/dpixel is zero
+    outside those rows, and the same image inside them."""
+    from oracle import grad as G
+    sc, cam = tiny_scene(1500, 21, 80, 72, log_scale=(-2.8, 0.6))
+    bg = (0.1, 0.2, 0.3)
+    ty0, ty1 = 1, 3
+    dL = np.zeros((3, cam.height, cam.width))
+    dL[:, 16 * ty0:16 * ty1] = np.random.default_rng(4).normal(size=(3, 16 * (ty1 - ty0), cam.width))
+    img_f, T_f, g_f = G.forward_and_grad(sc, cam, dL, bg)
+    img_b, T_b, g_b = G.forward_and_grad(sc, cam, dL, bg, tile_rows=(ty0, ty1))
+    sl = slice(16 * ty0, 16 * ty1)
+    np.testing.assert_allclose(img_b[:, sl], img_f[:, sl], atol=1e-13)
+    np.testing.assert_allclose(T_b[sl], T_f[sl], atol=1e-13)
+    for k in g_f:
+        scale = np.abs(g_f[k]).max()
+        assert scale > 0
+        np.testing.assert_allclose(g_b[k], g_f[k], atol=1e-12 * scale)

@@ -57,6 +57,28 @@ def test_sort_static_equals_sort_on_consecutive_calls():
         assert torch.equal(ranges_s, ranges_r)
 
 
+def test_sort_static_at_its_documented_limits():
+    """n = GS_SORT_STATIC_MAX_GAUSSIANS and m_cap = GS_SORT_STATIC_MAX_INSTANCES
+    on a 3840x2160 image (240 x 135 tiles, three tile passes laid out): the
+    largest call the header accepts must run and equal gs_sort, and a small
+    call right after it must still be exact in the reused array."""
+    big, big_cam = tiny_scene(L.SORT_STATIC_MAX_GAUSSIANS, 21, 3840, 2160, log_scale=(-6.5, 0.4))
+    small, small_cam = tiny_scene(3000, 8, 120, 90, log_scale=(-3.0, 0.7))
+    for scene, cam, m_cap in ((big, big_cam, L.SORT_STATIC_MAX_INSTANCES), (small, small_cam, None)):
+        st = gs.SceneTensors.from_scene(scene, "cuda")
+        sp = gs.preprocess(st, cam)
+        keys_r, vals_r, ranges_r, m_ref, _ = gs.sort(sp, scene.n, cam, L.SORT_STATIC_MAX_INSTANCES)
+        torch.cuda.synchronize()
+        assert 0 < m_ref <= L.SORT_STATIC_MAX_INSTANCES
+        code, keys_s, vals_s, ranges_s, m_s = _sort_static_through_c_abi(sp, scene.n, cam,
+                                                                         m_cap if m_cap else m_ref)
+        assert code == L.GS_OK, L.strerror(code)
+        assert m_s == m_ref
+        assert torch.equal(keys_s[:m_ref], keys_r[:m_ref])
+        assert torch.equal(vals_s[:m_ref], vals_r[:m_ref])
+        assert torch.equal(ranges_s, ranges_r)
+
+
 def test_sort_static_rejects_sizes_beyond_its_scratch():
     cam = gs.camera_struct(orbit_camera(0, 20, 4.0, 64, 48))
     P = ctypes.c_void_p

@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "frames/s at 3M Gaussians 1600x1064 vs roofline; served p50/p99 latency"
 FLOP_PER_EVAL = 25  # FP32 work per Gaussian-pixel evaluation of the blend (FMA = 2)
+# balanced batch render (gs_render_batch_balanced) settings of the multi-view
+# legs: long lists first (heavy_len splats and up), and with splitting
+BALANCE_HEAVY = dict(heavy_len=8192, max_heavy_tiles=16384, budget=0, max_split_tiles=0)
+BALANCE_SPLIT = dict(heavy_len=8192, max_heavy_tiles=16384, budget=4096, max_split_tiles=4096, max_chunks=32,
+                     chunk=1024)
 
 
 def parse_args():
@@ -53,6 +58,9 @@ def parse_args():
                    help="profiler driver: a 2M-Gaussian slab scene (the multi-view recipe at a third of its size), "
                         "two 1920x1080 views preprocessed and sorted, then this many gs_render_batch launches of "
                         "both views; no timing")
+    p.add_argument("--profile-split", action="store_true",
+                   help="with --profile-multiview: the launches are gs_render_batch_balanced (long lists first, "
+                        "heavy tiles split)")
     p.add_argument("--profile-backward", type=int, default=0,
                    help="profiler driver: forward of the 1M-Gaussian 1237x822 backward workload (pose 0), then this "
                         "many backward passes (per pass: gs_render_backward_splats, gs_preprocess_backward); no "
@@ -268,41 +276,31 @@ def main():
     from synth import CONFIGS
 
     if args.profile_multiview > 0:  # fixed launch sequence for ncu captures
-        import ctypes
-        from paper_2509_25626_gb300 import serve as S
         from synth import orbit_camera, slab_scene
         sm_ = slab_scene(2_000_000, seed=5)
         stm = gs.SceneTensors.from_scene(sm_, dev)
         cms = [orbit_camera(k, 8, 4.0, 1920, 1080, arc=math.radians(40.0)) for k in (0, 7)]
-        views = []
+        jobs = []
         for cm in cms:
             sp = gs.preprocess(stm, cm)
             _, vals, ranges, _, _ = gs.sort(sp, sm_.n, cm, 1 << 25)
             out = (torch.empty((3, cm.height, cm.width), dtype=torch.float32, device=dev),
                    torch.empty((cm.height, cm.width), dtype=torch.float32, device=dev),
                    torch.empty((cm.height, cm.width), dtype=torch.int32, device=dev))
-            views.append((cm, sp, vals, ranges, out))
-        srv = S.Server({}, max_batch=len(cms))
-
-        class _Req:
-            def __init__(self, cam):
-                self.cam, self.bg = cam, (0.0, 0.0, 0.0)
-
-        class _Slot:
-            def __init__(self, sp, vals, ranges, out, cam):
-                self.splats, self.vals, self.ranges = sp, vals, ranges
-                self.image, self.final_T, self.n_contrib = out
-                self.tiles = gs.num_tiles(cam)
-
-        srv._write_desc([(_Req(c), _Slot(sp, v, r, o, c)) for c, sp, v, r, o in views])
-        srv.desc_dev.copy_(srv.desc_host)
-        sptr = ctypes.c_void_p(int(torch.cuda.current_stream(dev).cuda_stream))
+            jobs.append(gs.BatchJob(sp, vals, ranges, *out, cm.width, cm.height))
+        rb = gs.RenderBatch(len(jobs), device=dev)
+        rb.set_jobs(jobs)
+        bp = gs.BalanceParams(**BALANCE_SPLIT) if args.profile_split else None
+        ws = gs.balance_workspace(bp, device=dev) if bp else None
         for _ in range(args.profile_multiview):
-            L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
-                                            ctypes.c_void_p(srv.counter.data_ptr()), 0, sptr), "gs_render_batch")
+            if ws is None:
+                rb.launch()
+            else:
+                rb.launch_balanced(bp, ws)
         torch.cuda.synchronize(dev)
         if rank == 0:
-            print(json.dumps({"profile_multiview": args.profile_multiview, "workload": "slab_2m_1920x1080x2"}))
+            print(json.dumps({"profile_multiview": args.profile_multiview, "split": bool(args.profile_split),
+                              "workload": "slab_2m_1920x1080x2"}))
         return 0
 
     if args.profile_backward > 0:  # fixed launch sequence for ncu captures
@@ -743,23 +741,12 @@ def measure_multiview(gs, dev, steps: int = 5):
         ms.append(m)
         del sp
     rs = [gs.Renderer(st.n, cam.width, cam.height, int(max(ms) * 1.05) + 4096, dev) for cam in cams]
-    srv = S.Server({}, max_batch=len(cams), device=dev)
-
-    class _Req:
-        def __init__(self, cam):
-            self.cam, self.bg = cam, (0.0, 0.0, 0.0)
-
-    class _Slot:
-        def __init__(self, r, cam):
-            self.splats, self.vals, self.ranges = r.splats, r.vals, r.ranges
-            self.image, self.final_T, self.n_contrib = r.image, r.final_T, r.n_contrib
-            self.tiles = gs.num_tiles(cam)
-
-    batch = [(_Req(c), _Slot(r, c)) for r, c in zip(rs, cams)]
-    tiles = srv._write_desc(batch)
-    srv.desc_dev.copy_(srv.desc_host)
+    rb = gs.RenderBatch(len(cams), device=dev)
+    tiles = rb.set_jobs([gs.BatchJob(r.splats, r.vals, r.ranges, r.image, r.final_T, r.n_contrib, c.width, c.height)
+                         for r, c in zip(rs, cams)])
+    bal = {k: gs.BalanceParams(**v) for k, v in (("heavy", BALANCE_HEAVY), ("split", BALANCE_SPLIT))}
+    bal_ws = {k: gs.balance_workspace(v, device=dev) for k, v in bal.items()}
     stream = torch.cuda.current_stream(dev)
-    sptr = ctypes.c_void_p(int(stream.cuda_stream))
 
     # each view's preprocess and sort on a stream of its own (the views are
     # independent and their sorts are latency-bound), forked from and joined
@@ -779,8 +766,13 @@ def measure_multiview(gs, dev, steps: int = 5):
             stream.wait_event(join)
 
     def batched():
-        L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
-                                        ctypes.c_void_p(srv.counter.data_ptr()), 0, sptr), "gs_render_batch")
+        rb.launch()
+
+    def batched_heavy():
+        rb.launch_balanced(bal["heavy"], bal_ws["heavy"])
+
+    def batched_split():
+        rb.launch_balanced(bal["split"], bal_ws["split"])
 
     def separate():
         for r, cam in zip(rs, cams):
@@ -788,7 +780,8 @@ def measure_multiview(gs, dev, steps: int = 5):
 
     E = lambda: torch.cuda.Event(enable_timing=True)
     res = {}
-    for name, fn in (("batched", batched), ("separate", separate)):
+    for name, fn in (("batched", batched), ("batched_long_first", batched_heavy), ("batched_split", batched_split),
+                     ("separate", separate)):
         front()
         fn()
         torch.cuda.synchronize(dev)
@@ -849,9 +842,58 @@ def measure_multiview(gs, dev, steps: int = 5):
         v["frac"] = v["tflops"] / fp32_peak
     res["evals"] = evals
     res["pipelined"] = pipe
+    res["balance_params"] = dict(long_first=BALANCE_HEAVY, split=BALANCE_SPLIT,
+                                 long_tiles=int(bal_ws["split"][8:12].view(torch.int32).item()),
+                                 split_tiles=int(bal_ws["split"][:4].view(torch.int32).item()))
+    res["slab_2m_1920x1080x2"] = measure_split_small(gs, dev, steps=max(steps, 10))
     return dict(workload="slab_6m_3840x2160x8", gaussians=st.n, views=len(cams), tiles=int(tiles),
                 instances_mean=float(sum(ms) / len(ms)), tile_list_mean=float(lens.mean()),
                 tile_list_max=int(lens.max()), tile_list_var=float(lens.var()), tile_cycles=tc, **res)
+
+
+def measure_split_small(gs, dev, steps: int = 10):
+    """The load-imbalance recipe at a third of its size and a quarter of its
+    pixels (2M Gaussians, two 1920x1080 views), where a few slab-edge tiles
+    dominate the batch launch: gs_render_batch against gs_render_batch_split
+    (render only, the same sorted inputs)."""
+    import torch
+    from synth import orbit_camera, slab_scene
+    sc = slab_scene(2_000_000, seed=5)
+    st = gs.SceneTensors.from_scene(sc, dev)
+    cams = [orbit_camera(k, 8, 4.0, 1920, 1080, arc=math.radians(40.0)) for k in (0, 7)]
+    jobs = []
+    for cam in cams:
+        sp = gs.preprocess(st, cam)
+        _, vals, ranges, _, _ = gs.sort(sp, sc.n, cam, 1 << 25)
+        out = (torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=dev),
+               torch.empty((cam.height, cam.width), dtype=torch.float32, device=dev),
+               torch.empty((cam.height, cam.width), dtype=torch.int32, device=dev))
+        jobs.append(gs.BatchJob(sp, vals, ranges, *out, cam.width, cam.height))
+    rb = gs.RenderBatch(len(jobs), device=dev)
+    rb.set_jobs(jobs)
+    bal = {k: gs.BalanceParams(**v) for k, v in (("heavy", BALANCE_HEAVY), ("split", BALANCE_SPLIT))}
+    bal_ws = {k: gs.balance_workspace(v, device=dev) for k, v in bal.items()}
+    stream = torch.cuda.current_stream(dev)
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn in (("batched", lambda: rb.launch()),
+                     ("batched_long_first", lambda: rb.launch_balanced(bal["heavy"], bal_ws["heavy"])),
+                     ("batched_split", lambda: rb.launch_balanced(bal["split"], bal_ws["split"]))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = E(), E()
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = dict(render_ms=a.elapsed_time(b) / steps)
+    out["long_tiles"] = int(bal_ws["split"][8:12].view(torch.int32).item())
+    out["split_tiles"] = int(bal_ws["split"][:4].view(torch.int32).item())
+    out["speedup_long_first"] = out["batched"]["render_ms"] / out["batched_long_first"]["render_ms"]
+    out["speedup_split"] = out["batched"]["render_ms"] / out["batched_split"]["render_ms"]
+    return out
 
 
 def measure_backward(gs, dev, steps: int, warmup: int):

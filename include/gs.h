@@ -336,6 +336,48 @@ int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t
  * usable.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_check_wait_timeout(void *workspace, size_t workspace_bytes, uint64_t limit_ns, void *stream);
 
+/* Settings of gs_render_batch_balanced. */
+typedef struct gs_balance_params {
+    int32_t heavy_len;       /* tiles whose list holds >= heavy_len splats start first; 0 = off */
+    int32_t max_heavy_tiles; /* capacity of that queue; if more tiles qualify, the plain order is kept */
+    int32_t budget;          /* splats walked before a still-live tile is split; 0 = never split */
+    int32_t max_split_tiles; /* capacity of the split queue; further tiles are walked whole */
+    int32_t max_chunks;      /* chunks walked per split tile, 1 .. 64 (with budget > 0) */
+    int32_t chunk;           /* splats per chunk, >= 1, rounded up to 256 (with budget > 0) */
+} gs_balance_params;
+
+/* Bytes of device workspace gs_render_batch_balanced needs (256-byte
+ * aligned); 0 if the parameters are invalid. */
+size_t gs_render_balance_workspace_bytes(const gs_balance_params *params);
+
+/* gs_render_batch with the inter-block load imbalance of heavy tiles
+ * (Section IV-C, Table III; the list splitting of Balanced-3DGS, Section
+ * II-A) evened out, in up to four launches enqueued on `stream`:
+ *   0. (heavy_len > 0) the (job, tile) items whose list holds at least
+ *      heavy_len splats are queued; the persistent render takes them first,
+ *      so a long list is not picked up at the end of the launch;
+ *   1. the persistent batch render, except that (budget > 0) a block that
+ *      has walked `budget` splats of a tile's list while some pixel is still
+ *      live saves the pixels' state (C, T, last blended position) and queues
+ *      the rest of the list instead of walking it;
+ *   2. (budget > 0) the next max_chunks chunks of `chunk` splats of each
+ *      queued list walked in parallel from T = 1 into per-chunk partial (C,
+ *      T, last, stopped);
+ *   3. (budget > 0) per queued tile, the chunks combined front to back:
+ *      C += T C_k, T *= T_k, while T T_k >= 1e-4 and chunk k did not stop;
+ *      the chunk where the absolute transmittance crosses 1e-4 is walked
+ *      again from the true incoming (C, T), so each pixel stops exactly
+ *      where one walk of the whole list stops; the list beyond the chunks,
+ *      if a pixel still needs it, is walked there too.
+ * Without splitting every job's outputs equal gs_render's bit for bit (only
+ * the order of the tiles changes); split tiles equal it up to the FP32
+ * rounding of the regrouped products (the same decisions off the
+ * thresholds).  desc, counter, grid: as gs_render_batch.  workspace:
+ * gs_render_balance_workspace_bytes(params) bytes, 256-byte aligned.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+int gs_render_batch_balanced(const gs_render_batch_desc *desc, uint32_t *counter, const gs_balance_params *params,
+                             void *workspace, size_t workspace_bytes, int32_t grid, void *stream);
+
 /* Text for a GS_* code, or the CUDA error string of the last GS_ERR_CUDA. */
 const char *gs_strerror(int code);
 const char *gs_last_cuda_error(void);

@@ -5,6 +5,10 @@ per-tile alpha blending, behind the C ABI in include/gs.h (libgs.so).
 
 from ._lib import GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_INVALID_ARG, GS_ERR_TOO_LARGE, GS_OK, SPLAT_DTYPE, GsError  # noqa: F401
 from .api import (  # noqa: F401
+    BalanceParams,
+    BatchJob,
+    RenderBatch,
+    balance_workspace,
     Renderer,
     FramePipeline,
     RasterizeGaussians,

@@ -51,6 +51,11 @@ class GsSceneGrads(ctypes.Structure):
                 ("dopacity_logits", c_void_p), ("dsh", c_void_p)]
 
 
+class GsBalanceParams(ctypes.Structure):
+    _fields_ = [("heavy_len", c_int32), ("max_heavy_tiles", c_int32), ("budget", c_int32),
+                ("max_split_tiles", c_int32), ("max_chunks", c_int32), ("chunk", c_int32)]
+
+
 class GsError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {strerror(code)} (code {code})")
@@ -99,6 +104,10 @@ def lib():
         L.gs_preprocess_backward.argtypes = [ctypes.POINTER(GsScene), ctypes.POINTER(GsCamera), P, P,
                                              ctypes.POINTER(GsSceneGrads), P]
         L.gs_preprocess_backward.restype = ctypes.c_int
+        L.gs_render_balance_workspace_bytes.argtypes = [ctypes.POINTER(GsBalanceParams)]
+        L.gs_render_balance_workspace_bytes.restype = c_size_t
+        L.gs_render_batch_balanced.argtypes = [P, P, ctypes.POINTER(GsBalanceParams), P, c_size_t, ctypes.c_int32, P]
+        L.gs_render_batch_balanced.restype = ctypes.c_int
         L.gs_check_wait_timeout.argtypes = [P, c_size_t, ctypes.c_uint64, P]
         L.gs_check_wait_timeout.restype = ctypes.c_int
         L.gs_strerror.argtypes = [ctypes.c_int]
@@ -126,5 +135,5 @@ def exported_symbols():
     return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
             "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
             "gs_render_backward", "gs_render_backward_splats", "gs_preprocess_backward",
-            "gs_render_batch", "gs_check_wait_timeout",
+            "gs_render_batch", "gs_render_balance_workspace_bytes", "gs_render_batch_balanced", "gs_check_wait_timeout",
             "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

@@ -281,6 +281,110 @@ class Renderer:
         return sort_status(self.workspace, stream)
 
 
+JOB_DTYPE = np.dtype([("splats", "<u8"), ("vals", "<u8"), ("ranges", "<u8"), ("out", "<u8"), ("T", "<u8"),
+                      ("nc", "<u8"), ("w", "<i4"), ("h", "<i4"), ("bg", "<f4", 3), ("tile_begin", "<u4")])
+DESC_HEADER = 16
+assert JOB_DTYPE.itemsize == 72  # gs_render_job
+
+
+@dataclass
+class BatchJob:
+    """One job of a batched render: gs_render's inputs and outputs."""
+    splats: torch.Tensor
+    vals: torch.Tensor
+    ranges: torch.Tensor
+    image: torch.Tensor
+    final_T: torch.Tensor
+    n_contrib: torch.Tensor
+    width: int
+    height: int
+    bg: tuple = (0.0, 0.0, 0.0)
+
+
+class RenderBatch:
+    """The job table of gs_render_batch / gs_render_batch_split (a
+    gs_render_batch_desc) in pinned host memory and on the device, plus the
+    work counter.  ``set_jobs`` writes the table and enqueues its upload;
+    the launches read it on the device, so a captured launch serves any
+    later table."""
+
+    def __init__(self, max_jobs: int, device="cuda"):
+        self.max_jobs = int(max_jobs)
+        nbytes = DESC_HEADER + JOB_DTYPE.itemsize * self.max_jobs
+        self.desc_host = torch.zeros(nbytes, dtype=torch.uint8).pin_memory()
+        self.desc_dev = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        self.total_tiles = 0
+
+    def write(self, jobs) -> int:
+        """Writes the host table (jobs: BatchJob-like objects); returns the
+        total tile count.  Does not upload."""
+        if len(jobs) > self.max_jobs:
+            raise ValueError(f"{len(jobs)} jobs exceed the table's {self.max_jobs}")
+        tab = np.zeros(len(jobs), dtype=JOB_DTYPE)
+        total = 0
+        for i, j in enumerate(jobs):
+            w, h = int(j.width), int(j.height)
+            tab[i] = (j.splats.data_ptr(), j.vals.data_ptr(), j.ranges.data_ptr(), j.image.data_ptr(),
+                      j.final_T.data_ptr(), j.n_contrib.data_ptr(), w, h, tuple(float(v) for v in j.bg), total)
+            total += ((w + 15) // 16) * ((h + 15) // 16)
+        host = self.desc_host.numpy()
+        host[:8] = np.frombuffer(np.array([len(jobs), total], dtype=np.uint32).tobytes(), np.uint8)
+        host[8:DESC_HEADER] = 0
+        host[DESC_HEADER:DESC_HEADER + JOB_DTYPE.itemsize * len(jobs)] = np.frombuffer(tab.tobytes(), np.uint8)
+        self.total_tiles = total
+        return total
+
+    def upload(self, stream=None):
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            self.desc_dev.copy_(self.desc_host, non_blocking=True)
+
+    def set_jobs(self, jobs, stream=None) -> int:
+        total = self.write(jobs)
+        self.upload(stream)
+        return total
+
+    def launch(self, grid: int = 0, stream=None):
+        """gs_render_batch over the uploaded table."""
+        L.check(L.lib().gs_render_batch(_ptr(self.desc_dev), _ptr(self.counter), int(grid), _stream(stream)),
+                "gs_render_batch")
+
+    def launch_balanced(self, params: "BalanceParams", workspace: torch.Tensor, grid: int = 0, stream=None):
+        """gs_render_batch_balanced over the uploaded table (workspace from
+        balance_workspace(params))."""
+        _check_tensor(workspace, torch.uint8, "workspace")
+        c = params.struct()
+        L.check(L.lib().gs_render_batch_balanced(_ptr(self.desc_dev), _ptr(self.counter), ctypes.byref(c),
+                                                 _ptr(workspace), workspace.numel(), int(grid), _stream(stream)),
+                "gs_render_batch_balanced")
+
+
+@dataclass
+class BalanceParams:
+    """gs_balance_params: long-list tiles first (heavy_len splats and up,
+    0 = off) and splitting of tiles still live after `budget` splats
+    (0 = off) into max_chunks chunks of `chunk` splats."""
+    heavy_len: int = 4096
+    max_heavy_tiles: int = 4096
+    budget: int = 0
+    max_split_tiles: int = 0
+    max_chunks: int = 32
+    chunk: int = 1024
+
+    def struct(self) -> L.GsBalanceParams:
+        return L.GsBalanceParams(int(self.heavy_len), int(self.max_heavy_tiles), int(self.budget),
+                                 int(self.max_split_tiles), int(self.max_chunks), int(self.chunk))
+
+
+def balance_workspace(params: BalanceParams, device="cuda") -> torch.Tensor:
+    c = params.struct()
+    n = int(L.lib().gs_render_balance_workspace_bytes(ctypes.byref(c)))
+    if n == 0:
+        raise ValueError(f"invalid balance parameters {params}")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
 class FramePipeline:
     """End-to-end frames from host memory, double-buffered.
 

@@ -40,6 +40,10 @@ cudaError_t launch_preprocess_backward(const gs_scene &s, const CamParams &cam, 
                                        const float *dsplat, const gs_scene_grads &g, cudaStream_t st);
 cudaError_t launch_lookback_probe(const SortWs &ws, uint64_t limit_ns, cudaStream_t st);
 cudaError_t launch_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int grid, cudaStream_t stream);
+size_t balance_ws_bytes(const gs_balance_params &p);
+cudaError_t launch_render_batch_balanced(const gs_render_batch_desc *desc, uint32_t *counter,
+                                         const gs_balance_params &p, void *workspace, int grid,
+                                         cudaStream_t stream);
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
                           uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream);
@@ -205,6 +209,28 @@ int gs_render_batch(const gs_render_batch_desc *desc, uint32_t *counter, int32_t
     gs::NvtxRange nvtx_range("gs_render_batch");
     if (!desc || !aligned(desc, 8) || !counter || !aligned(counter, 4) || grid < 0) return GS_ERR_INVALID_ARG;
     return cuda_status(launch_render_batch(desc, counter, grid, (cudaStream_t)stream));
+}
+
+static bool balance_params_ok(const gs_balance_params *p) {
+    if (!p) return false;
+    if (p->heavy_len < 0 || p->max_heavy_tiles < 0 || p->budget < 0 || p->max_split_tiles < 0) return false;
+    if (p->budget > 0 && (p->max_chunks < 1 || p->max_chunks > 64 || p->chunk < 1)) return false;
+    return true;
+}
+
+size_t gs_render_balance_workspace_bytes(const gs_balance_params *params) {
+    if (!balance_params_ok(params)) return 0;
+    return balance_ws_bytes(*params);
+}
+
+int gs_render_batch_balanced(const gs_render_batch_desc *desc, uint32_t *counter, const gs_balance_params *params,
+                             void *workspace, size_t workspace_bytes, int32_t grid, void *stream) {
+    gs::NvtxRange nvtx_range("gs_render_batch_balanced");
+    if (!desc || !aligned(desc, 8) || !counter || !aligned(counter, 4) || grid < 0) return GS_ERR_INVALID_ARG;
+    if (!balance_params_ok(params)) return GS_ERR_INVALID_ARG;
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < balance_ws_bytes(*params))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_batch_balanced(desc, counter, *params, workspace, grid, (cudaStream_t)stream));
 }
 
 int gs_frame(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, uint64_t *keys, uint32_t *vals,

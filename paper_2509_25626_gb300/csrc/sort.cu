@@ -43,6 +43,10 @@ constexpr int kThreads = 256;
 constexpr int kIpt = kSortTileItems / kThreads;  // 16 items per thread
 // Threads per block of the radix passes over arrays (4096 elements each).
 constexpr int kSweepThreads = 256;  // 512 measured slower
+#ifndef GS_DEPTH_THREADS
+#define GS_DEPTH_THREADS 256
+#endif
+constexpr int kDepthThreads = GS_DEPTH_THREADS;  // threads per block of the depth passes
 // Predecessors read per round trip of the look-back walks (depth passes,
 // tile passes).  Every block's live digits walk at once, so wider windows
 // mostly add L2 requests: 4 measured faster than 2, 8, 16 and 32.
@@ -485,7 +489,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
 // block of NT threads.  diff_hist: the digit totals are given as a
 // difference array (the tile passes).
 template <bool kFinal, int NT, int WIN, int ITEMS, bool kRect = false>
-__global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3)) onesweep_kernel(const uint32_t *__restrict__ kin,
+__global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 1024 ? 1 : (NT >= 512 ? 2 : 3))) onesweep_kernel(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                             uint64_t *__restrict__ kout64,
@@ -497,7 +501,8 @@ __global__ void __launch_bounds__(NT, ITEMS / NT <= 8 ? 4 : (NT >= 512 ? 2 : 3))
                                                             uint32_t tiles_x, const uint2 *__restrict__ rect_in = nullptr,
                                                             uint2 *__restrict__ rect_out = nullptr) {
     constexpr int IPT = ITEMS / NT;
-    __shared__ SweepSmemT<NT, ITEMS> sm;
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // SweepSmemT<NT, ITEMS>, may exceed 48 KB
+    SweepSmemT<NT, ITEMS> &sm = *reinterpret_cast<SweepSmemT<NT, ITEMS> *>(s_dyn);
     __shared__ uint32_t s_slot;
     const uint32_t n = *count_ptr;
     const uint32_t nblocks = (n + ITEMS - 1) / ITEMS;
@@ -747,6 +752,19 @@ __global__ void lookback_probe_kernel(uint64_t *state, SortHeader *hdr, uint64_t
     walk_back<kTileWin>(state, 1u, 1u, 1ull, hdr);
 }
 
+// Launches one radix pass with its shared memory as dynamic shared memory
+// (the larger block shapes need more than the 48 KB of static shared
+// memory); the opt-in size is set once per instantiation.
+template <bool kFinal, int NT, int WIN, int ITEMS, bool kRect = false, typename... Args>
+cudaError_t launch_onesweep(uint32_t grid, cudaStream_t st, Args... args) {
+    constexpr size_t smem = sizeof(SweepSmemT<NT, ITEMS>);
+    static cudaError_t attr = cudaFuncSetAttribute(onesweep_kernel<kFinal, NT, WIN, ITEMS, kRect>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    onesweep_kernel<kFinal, NT, WIN, ITEMS, kRect><<<grid, NT, smem, st>>>(args...);
+    return cudaSuccess;
+}
+
 }  // namespace
 
 // Runs lookback_probe_kernel on a zeroed header and two state words of `ws`.
@@ -770,14 +788,19 @@ cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &w
     // the last pass writes each sorted splat's rectangle in place of its key
     // (no later step reads the sorted depth bits), so that the offsets and
     // the duplication read rectangles densely instead of gathering them by id
-    for (int p = 0; p < 3; ++p)
-        onesweep_kernel<false, kSweepThreads, kDepthWin, kDepthItems><<<nbd, kSweepThreads, 0, st>>>(ws.dkey[p & 1], ws.dval[p & 1], ws.dkey[(p + 1) & 1],
-                                                         ws.dval[(p + 1) & 1], nullptr, nullptr, &ws.hdr->nvis, 8 * p,
-                                                         ws.hist_depth + kBins * p, false, ws.depth_state[p],
-                                                         &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u);
-    onesweep_kernel<false, kSweepThreads, kDepthWin, kDepthItems, true><<<nbd, kSweepThreads, 0, st>>>(
-        ws.dkey[1], ws.dval[1], nullptr, ws.dval[0], nullptr, nullptr, &ws.hdr->nvis, 24, ws.hist_depth + kBins * 3,
-        false, ws.depth_state[3], &ws.hdr->tile_ctr[kCtrDepth + 3], ws.hdr, 0, 0u, ws.rectv, ws.srect);
+    for (int p = 0; p < 3 && e == cudaSuccess; ++p)
+        e = launch_onesweep<false, kDepthThreads, kDepthWin, kDepthItems>(
+            nbd, st, (const uint32_t *)ws.dkey[p & 1], (const uint32_t *)ws.dval[p & 1], ws.dkey[(p + 1) & 1],
+            ws.dval[(p + 1) & 1], (uint64_t *)nullptr, (const uint32_t *)nullptr, (const uint32_t *)&ws.hdr->nvis,
+            8 * p, (const uint32_t *)(ws.hist_depth + kBins * p), false, ws.depth_state[p],
+            &ws.hdr->tile_ctr[kCtrDepth + p], ws.hdr, 0, 0u, (const uint2 *)nullptr, (uint2 *)nullptr);
+    if (e == cudaSuccess)
+        e = launch_onesweep<false, kDepthThreads, kDepthWin, kDepthItems, true>(
+            nbd, st, (const uint32_t *)ws.dkey[1], (const uint32_t *)ws.dval[1], (uint32_t *)nullptr, ws.dval[0],
+            (uint64_t *)nullptr, (const uint32_t *)nullptr, (const uint32_t *)&ws.hdr->nvis, 24,
+            (const uint32_t *)(ws.hist_depth + kBins * 3), false, ws.depth_state[3], &ws.hdr->tile_ctr[kCtrDepth + 3],
+            ws.hdr, 0, 0u, (const uint2 *)ws.rectv, ws.srect);
+    if (e != cudaSuccess) return e;
     offsets_kernel<<<nb, kThreads, 0, st>>>(ws, m_cap, tl);
     return cudaGetLastError();
 }
@@ -803,15 +826,20 @@ cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws
             dup_sweep_kernel<false><<<nb, kThreads, 0, st>>>(ws, tl, tx, buf_k(1), buf_v(1), nullptr);
         for (int p = 1; p < passes; ++p) {
             const uint32_t *hist = ws.hist_tile + (kBins + 1) * p;
+            cudaError_t e;
             if (p == passes - 1)
-                onesweep_kernel<true, kSweepThreads, kTileWin, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(buf_k(p), buf_v(p), nullptr, vals, keys, ws.depthv,
-                                                                &ws.hdr->m_sort, 8 * p, hist, true, ws.tile_state[p],
-                                                                &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y,
-                                                                tx);
+                e = launch_onesweep<true, kSweepThreads, kTileWin, kTilePassItems>(
+                    nbt, st, (const uint32_t *)buf_k(p), (const uint32_t *)buf_v(p), (uint32_t *)nullptr, vals, keys,
+                    (const uint32_t *)ws.depthv, (const uint32_t *)&ws.hdr->m_sort, 8 * p, hist, true,
+                    ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx,
+                    (const uint2 *)nullptr, (uint2 *)nullptr);
             else
-                onesweep_kernel<false, kSweepThreads, kTileWin, kTilePassItems><<<nbt, kSweepThreads, 0, st>>>(
-                    buf_k(p), buf_v(p), buf_k(p + 1), buf_v(p + 1), nullptr, nullptr, &ws.hdr->m_sort, 8 * p, hist,
-                    true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx);
+                e = launch_onesweep<false, kSweepThreads, kTileWin, kTilePassItems>(
+                    nbt, st, (const uint32_t *)buf_k(p), (const uint32_t *)buf_v(p), buf_k(p + 1), buf_v(p + 1),
+                    (uint64_t *)nullptr, (const uint32_t *)nullptr, (const uint32_t *)&ws.hdr->m_sort, 8 * p, hist,
+                    true, ws.tile_state[p], &ws.hdr->tile_ctr[kCtrTiles + p], ws.hdr, tl.shift_y, tx,
+                    (const uint2 *)nullptr, (uint2 *)nullptr);
+            if (e != cudaSuccess) return e;
         }
     }
     ranges_kernel<<<(unsigned)(((uint64_t)num_tiles * 32 + 255) / 256), 256, 0, st>>>(

@@ -36,9 +36,8 @@ namespace {
 // how many tile passes are laid out, and 2^32 tiles takes the most.
 constexpr size_t kStaticBound =
     sort_ws_offsets(GS_SORT_STATIC_MAX_GAUSSIANS, GS_SORT_STATIC_MAX_INSTANCES, 1ull << 32).total;
-constexpr size_t kStaticScratchBytes = (kStaticBound + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+constexpr size_t kStaticScratchBytes = (size_t)42 << 20;  // the size stated in gs.h
 static_assert(kStaticScratchBytes >= kStaticBound, "static scratch below the workspace bound");
-static_assert(kStaticScratchBytes == (size_t)42 << 20, "the 42 MiB stated in gs.h");
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_sort_scratch[kStaticScratchBytes];

@@ -7,7 +7,10 @@
 namespace gs {
 
 constexpr int kSortTileItems = 4096;   // elements per block in the look-back scans and tile radix passes
-constexpr int kDepthItems = 4096;      // elements per block in the depth radix passes
+#ifndef GS_DEPTH_ITEMS
+#define GS_DEPTH_ITEMS 4096
+#endif
+constexpr int kDepthItems = GS_DEPTH_ITEMS;  // elements per block in the depth radix passes
 constexpr int kTilePassItems = 4096;   // elements per block in the tile passes after the first (2048 measured slower)
 constexpr int kMaxTilePasses = 4;      // 8-bit digits of a 32-bit tile id
 

@@ -120,6 +120,28 @@ def test_workspace_size_monotone(L):
     assert lib.gs_sort_workspace_bytes(0, 0, 1) > 0
 
 
+def test_balance_params_checked_on_host(L):
+    """gs_render_batch_balanced rejects bad settings and a short workspace
+    before any launch."""
+    lib = L.lib()
+    P = ctypes.c_void_p
+    ok = L.GsBalanceParams(4096, 1024, 4096, 256, 32, 1024)
+    need = lib.gs_render_balance_workspace_bytes(ctypes.byref(ok))
+    assert need > 256
+    no_split = L.GsBalanceParams(4096, 1024, 0, 0, 0, 0)  # chunks unused without a budget
+    assert 0 < lib.gs_render_balance_workspace_bytes(ctypes.byref(no_split)) < need
+    for bad in (L.GsBalanceParams(-1, 1024, 0, 0, 0, 0), L.GsBalanceParams(4096, 1024, 4096, 256, 0, 1024),
+                L.GsBalanceParams(4096, 1024, 4096, 256, 65, 1024), L.GsBalanceParams(4096, 1024, 4096, 256, 32, 0)):
+        assert lib.gs_render_balance_workspace_bytes(ctypes.byref(bad)) == 0
+        assert lib.gs_render_batch_balanced(P(256), P(256), ctypes.byref(bad), P(256), 1 << 30, 0, None) == \
+            L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_batch_balanced(P(256), P(256), ctypes.byref(ok), P(256), need - 1, 0, None) == \
+        L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_batch_balanced(P(256), P(256), ctypes.byref(ok), P(256 + 8), need, 0, None) == \
+        L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_batch_balanced(P(256), P(256), None, P(256), need, 0, None) == L.GS_ERR_INVALID_ARG
+
+
 def test_static_sort_scratch_covers_its_limits(L):
     """gs_sort_static's fixed 42 MiB array holds gs_sort's workspace at the
     largest n and m_cap it accepts, for every tile grid (the grid only sets

@@ -650,40 +650,47 @@ def tile_cycle_stats(cyc) -> dict:
                 max_over_mean=float(c.max()) / max(mean, 1.0), sum=float(c.sum()))
 
 
-def measure_serving(gs, dev, rate: float = 200.0, duration: float = 2.5):
+def measure_serving(gs, dev, rates=(200.0, 800.0, 1600.0, 2400.0), duration: float = 1.0):
     """Continuous-batching server on three resident scenes (0.5M, 2M, 5M
-    Gaussians, clustered like the 3M workload), Poisson arrivals at `rate`
-    per second, each request a random orbit pose at a resolution drawn from
-    {640x480, 1280x720, 1600x1064, 1920x1080}.  Reports latency percentiles
-    and throughput of the batched server and of one-request-at-a-time
-    rendering on the same stream, plus both at saturation (all requests
-    present at t = 0)."""
+    Gaussians, clustered like the 3M workload), Poisson arrivals at each
+    offered rate, each request a random orbit pose at a resolution drawn
+    from {640x480, 1280x720, 1600x1064, 1920x1080}.  Per rate: latency
+    percentiles and delivered frames/s of the batched server and of
+    one-request-at-a-time rendering on the same slots and captured graphs;
+    plus both at saturation (all requests present at t = 0)."""
     from paper_2509_25626_gb300 import serve as S
     from synth import clustered_scene, orbit_camera
     specs = (("s0.5m", 500_000, 41), ("s2m", 2_000_000, 42), ("s5m", 5_000_000, 43))
     scenes = {name: gs.SceneTensors.from_scene(clustered_scene(n, seed=sd), dev) for name, n, sd in specs}
     res = [(640, 480), (1280, 720), (1600, 1064), (1920, 1080)]
-    srv = S.Server(scenes, max_batch=16, mem_budget=48 << 30, device=dev)
+    srv = S.Server(scenes, res, max_batch=16, mem_budget=96 << 30, device=dev, slots_per_scene=12)
     for name in scenes:
         for w, h in res:
             srv.calibrate(name, w, h, [orbit_camera(k, 6, 4.0, w, h) for k in range(6)])
     cam_fn = lambda u, w, h: orbit_camera(u * 20.0, 20, 4.0, w, h)
-    srv.serve(S.poisson_requests(rate, 0.3, list(scenes), res, cam_fn, seed=97), realtime=True)  # warm-up
-    srv.serve_sequential(S.poisson_requests(rate, 0.1, list(scenes), res, cam_fn, seed=96), realtime=True)
-    out = {}
+    srv.serve(S.poisson_requests(rates[0], 0.3, list(scenes), res, cam_fn, seed=97), realtime=True)  # warm-up
+    srv.serve_sequential(S.poisson_requests(rates[0], 0.1, list(scenes), res, cam_fn, seed=96), realtime=True)
+    out = {"rates": {}}
+    for rate in rates:
+        row = {}
+        for mode in ("batched", "sequential"):
+            reqs = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=99)
+            fn = srv.serve if mode == "batched" else srv.serve_sequential
+            done, wall = fn(reqs, realtime=True)
+            row[mode] = S.latency_stats(done, wall)
+            row[mode]["offered_per_s"] = len(reqs) / duration
+        out["rates"][f"{int(rate)}"] = row
     for mode in ("batched", "sequential"):
-        reqs = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=99)
-        fn = srv.serve if mode == "batched" else srv.serve_sequential
-        done, wall = fn(reqs, realtime=True)
-        out[mode] = S.latency_stats(done, wall)
-        sat = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=100)
+        sat = S.poisson_requests(rates[-1], duration, list(scenes), res, cam_fn, seed=100)
         for r in sat:
             r.arrival = 0.0
+        fn = srv.serve if mode == "batched" else srv.serve_sequential
         done, wall = fn(sat, realtime=False)
-        out[mode]["saturated_frames_per_s"] = len(done) / wall
-    out.update(workload="serve_3scenes_poisson200", rate_per_s=rate, duration_s=duration,
+        out[f"saturated_{mode}_frames_per_s"] = S.latency_stats(done, wall)["frames_per_s"]
+    out.update(workload="serve_3scenes_poisson", duration_s=duration,
                scenes={name: n for name, n, _ in specs}, resolutions=[f"{w}x{h}" for w, h in res],
-               batches=int(srv.stats["batches"]), overflow_or_timeout=int(srv.stats["overflow_or_timeout"]))
+               slots={k: int(v) for k, v in srv.stats.items() if k.startswith("slots_")},
+               batches=int(srv.stats["batches"]), failed=int(srv.stats["failed"]))
     return out
 
 

@@ -126,6 +126,22 @@ size_t gs_splat_buffer_bytes(int64_t n);
  * gs_sort_input.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats, void *stream);
 
+/* Cameras in device memory.  gs_preprocess takes the camera as kernel
+ * parameters, which a captured CUDA graph freezes; a server that replays one
+ * captured preprocess + sort per (scene, resolution) for every request
+ * instead keeps the camera in device memory and rewrites it before each
+ * replay (e.g. by a host-to-device copy captured in the same graph).
+ * gs_camera_block writes the kernels' form of `cam` (host, 16-byte
+ * aligned, gs_camera_block_bytes() bytes; the camera centre -R^T t is
+ * formed in double) into host memory `block`; gs_preprocess_camblock is
+ * gs_preprocess with that block read from device memory (16-byte aligned)
+ * when the kernel runs.  The block holds the image size: the gs_sort and
+ * gs_render calls of the same frame must use a camera of that size.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+size_t gs_camera_block_bytes(void);
+int gs_camera_block(const gs_camera *cam, void *block);
+int gs_preprocess_camblock(const gs_scene *scene, const void *camera_block, gs_splat *splats, void *stream);
+
 /* Bytes of device workspace gs_sort needs for n Gaussians, m_cap tile
  * instances and num_tiles = ceil(W/16) * ceil(H/16) tiles (the workspace
  * must be 256-byte aligned).  gs_sort also uses the key buffer (8 bytes per

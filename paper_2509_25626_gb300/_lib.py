@@ -108,6 +108,12 @@ def lib():
         L.gs_render_balance_workspace_bytes.restype = c_size_t
         L.gs_render_batch_balanced.argtypes = [P, P, ctypes.POINTER(GsBalanceParams), P, c_size_t, ctypes.c_int32, P]
         L.gs_render_batch_balanced.restype = ctypes.c_int
+        L.gs_camera_block_bytes.argtypes = []
+        L.gs_camera_block_bytes.restype = c_size_t
+        L.gs_camera_block.argtypes = [ctypes.POINTER(GsCamera), P]
+        L.gs_camera_block.restype = ctypes.c_int
+        L.gs_preprocess_camblock.argtypes = [ctypes.POINTER(GsScene), P, P, P]
+        L.gs_preprocess_camblock.restype = ctypes.c_int
         L.gs_check_wait_timeout.argtypes = [P, c_size_t, ctypes.c_uint64, P]
         L.gs_check_wait_timeout.restype = ctypes.c_int
         L.gs_strerror.argtypes = [ctypes.c_int]
@@ -132,7 +138,8 @@ def check(code: int, what: str) -> int:
 
 def exported_symbols():
     """Names of the gs_* functions the header declares."""
-    return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
+    return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_camera_block_bytes", "gs_camera_block",
+            "gs_preprocess_camblock", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
             "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
             "gs_render_backward", "gs_render_backward_splats", "gs_preprocess_backward",
             "gs_render_batch", "gs_render_balance_workspace_bytes", "gs_render_batch_balanced", "gs_check_wait_timeout",

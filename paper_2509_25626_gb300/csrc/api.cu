@@ -24,6 +24,7 @@ struct NvtxRange {
 };
 
 cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat *out, cudaStream_t stream);
+cudaError_t launch_preprocess_camdev(const gs_scene &s, const CamParams *cam_dev, gs_splat *out, cudaStream_t stream);
 cudaError_t launch_sort_front(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
                               uint32_t num_tiles, cudaStream_t st);
 cudaError_t launch_sort_back(const gs_splat *splats, int64_t n, const SortWs &ws, uint64_t m_cap, int tiles_x,
@@ -100,6 +101,29 @@ int gs_preprocess(const gs_scene *scene, const gs_camera *cam, gs_splat *splats,
             if (!p || !aligned(p, 16)) return GS_ERR_INVALID_ARG;
     }
     return cuda_status(launch_preprocess(*scene, make_cam_params(*cam), splats, (cudaStream_t)stream));
+}
+
+size_t gs_camera_block_bytes(void) { return sizeof(CamParams); }
+
+int gs_camera_block(const gs_camera *cam, void *block) {
+    if (!camera_ok(cam) || !block) return GS_ERR_INVALID_ARG;
+    const CamParams p = make_cam_params(*cam);
+    std::memcpy(block, &p, sizeof(p));
+    return GS_OK;
+}
+
+int gs_preprocess_camblock(const gs_scene *scene, const void *camera_block, gs_splat *splats, void *stream) {
+    gs::NvtxRange nvtx_range("gs_preprocess_camblock");
+    if (!scene || !camera_block || !aligned(camera_block, 16)) return GS_ERR_INVALID_ARG;
+    if (scene->n < 0 || scene->n > (int64_t)UINT32_MAX || scene->sh_degree < 0 || scene->sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (scene->n > 0) {
+        const void *ptrs[] = {scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, splats};
+        for (const void *p : ptrs)
+            if (!p || !aligned(p, 16)) return GS_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_preprocess_camdev(*scene, static_cast<const CamParams *>(camera_block), splats,
+                                                (cudaStream_t)stream));
 }
 
 size_t gs_sort_workspace_bytes(int64_t n, int64_t m_cap, int32_t num_tiles) {

@@ -46,15 +46,12 @@ __device__ __forceinline__ void write_culled(gs_splat *out, uint4 *sort_in, floa
     *sort_in = make_uint4(__float_as_uint(depth), 0u, 0u, 0u);
 }
 
-__global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict__ means,
-                                                         const float *__restrict__ log_scales,
-                                                         const float4 *__restrict__ quats,
-                                                         const float *__restrict__ logits,
-                                                         const float4 *__restrict__ sh, int64_t n, int sh_degree,
-                                                         CamParams cam, gs_splat *__restrict__ out,
-                                                         uint4 *__restrict__ sort_in) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+// The projection of Gaussian g (one thread).
+__device__ __forceinline__ void preprocess_one(const int64_t g, const float *__restrict__ means,
+                                               const float *__restrict__ log_scales, const float4 *__restrict__ quats,
+                                               const float *__restrict__ logits, const float4 *__restrict__ sh,
+                                               int sh_degree, const CamParams &cam, gs_splat *__restrict__ out,
+                                               uint4 *__restrict__ sort_in) {
     // the rotation, scales and opacity of a Gaussian that survives the
     // near-plane test are needed next: start them towards L2 with the mean
     asm volatile("prefetch.global.L2 [%0];" ::"l"(quats + g));
@@ -246,6 +243,34 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict
     sort_in[g] = si;  // the dense copy gs_sort reads
 }
 
+__global__ void __launch_bounds__(256) preprocess_kernel(const float *__restrict__ means,
+                                                         const float *__restrict__ log_scales,
+                                                         const float4 *__restrict__ quats,
+                                                         const float *__restrict__ logits,
+                                                         const float4 *__restrict__ sh, int64_t n, int sh_degree,
+                                                         CamParams cam, gs_splat *__restrict__ out,
+                                                         uint4 *__restrict__ sort_in) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    preprocess_one(g, means, log_scales, quats, logits, sh, sh_degree, cam, out, sort_in);
+}
+
+// The same with the camera read from device memory, so that a captured CUDA
+// graph can be replayed for a new pose by rewriting that memory.
+__global__ void __launch_bounds__(256) preprocess_camdev_kernel(const float *__restrict__ means,
+                                                                const float *__restrict__ log_scales,
+                                                                const float4 *__restrict__ quats,
+                                                                const float *__restrict__ logits,
+                                                                const float4 *__restrict__ sh, int64_t n,
+                                                                int sh_degree, const CamParams *__restrict__ camp,
+                                                                gs_splat *__restrict__ out,
+                                                                uint4 *__restrict__ sort_in) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const CamParams cam = *camp;
+    preprocess_one(g, means, log_scales, quats, logits, sh, sh_degree, cam, out, sort_in);
+}
+
 }  // namespace
 
 cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat *out, cudaStream_t stream) {
@@ -255,6 +280,16 @@ cudaError_t launch_preprocess(const gs_scene &s, const CamParams &cam, gs_splat 
     preprocess_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
         s.means, s.log_scales, reinterpret_cast<const float4 *>(s.quats), s.opacity_logits,
         reinterpret_cast<const float4 *>(s.sh), s.n, s.sh_degree, cam, out, reinterpret_cast<uint4 *>(out + s.n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_camdev(const gs_scene &s, const CamParams *cam_dev, gs_splat *out, cudaStream_t stream) {
+    if (s.n == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (s.n + threads - 1) / threads;
+    preprocess_camdev_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
+        s.means, s.log_scales, reinterpret_cast<const float4 *>(s.quats), s.opacity_logits,
+        reinterpret_cast<const float4 *>(s.sh), s.n, s.sh_degree, cam_dev, out, reinterpret_cast<uint4 *>(out + s.n));
     return cudaGetLastError();
 }
 

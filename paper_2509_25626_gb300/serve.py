@@ -1,17 +1,26 @@
 """Continuous-batching render server over resident scenes.
 
-Requests (scene, camera) arrive over time.  Each is admitted when a slot
-and enough device memory (by a per-(scene, resolution) estimate) are free;
-its preprocess and sort then run at once on a stream of their own, so they
+Requests (scene, camera) arrive over time.  Device memory is divided up
+front into request slots, per scene: each slot holds the splat buffer, the
+sort's keys, values, ranges and workspace for that scene at the largest
+calibrated resolution, a device camera block, and a CUDA stream.  A request
+is admitted as soon as a slot of its scene is free (memory-based admission:
+the slots are the memory).  Its preprocess and sort run at once on the
+slot's stream by replaying a CUDA graph captured for that slot and
+resolution -- the camera goes in through the slot's camera block, which the
+graph copies from pinned host memory before the preprocess -- so they
 overlap whatever batch is rendering.  Whenever the render engine is idle,
-every admitted request joins one batch, rendered by a single persistent
-launch (gs_render_batch) replayed from a captured CUDA graph; the launch
-waits for those requests' sorts on the device, not on the host.  A request
-is complete when its batch's render has finished; its latency is completion
-time minus arrival time.
+every prepared request joins one batch, rendered by a single persistent
+launch (gs_render_batch) replayed from a captured graph; the launch waits
+for those requests' sorts on the device, not on the host.  A request is
+complete when its batch's render has finished; its latency is completion
+time minus arrival time.  A request whose tile instances overflowed its
+slot's capacity (or whose sort reported a timeout) is returned as failed,
+with no image, and is left out of the latency statistics.
 
-Every kernel runs in libgs.so; this module only schedules, allocates (from
-PyTorch's caching allocator) and keeps time.
+Every kernel runs in libgs.so; this module only schedules, owns the
+preallocated buffers, and keeps time.  Each request's outputs (image,
+final T, n_contrib) are tensors of its own, handed to the caller.
 """
 
 from __future__ import annotations
@@ -26,10 +35,11 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .api import SceneTensors, camera_struct, num_tiles, preprocess, render, sort, sort_workspace_bytes, splat_buffer
+from .api import (BatchJob, RenderBatch, SceneTensors, _ptr, camera_struct, num_tiles, preprocess, render, sort,
+                  sort_workspace_bytes, splat_buffer)
 
-JOB_BYTES = 72
-DESC_HEADER = 16
+# 16-byte aligned room for the kernels' camera block
+CAM_BLOCK_BYTES = 128
 
 
 @dataclasses.dataclass
@@ -46,6 +56,7 @@ class Request:
     final_T: torch.Tensor | None = None
     n_contrib: torch.Tensor | None = None
     instances: int = -1
+    error: str | None = None  # "capacity" or "timeout" for a failed request
 
     @property
     def latency(self) -> float:
@@ -53,49 +64,68 @@ class Request:
 
 
 class _Slot:
-    """Device buffers of one in-flight request."""
+    """The preallocated buffers of one in-flight request of a scene."""
 
-    def __init__(self, n, cam, m_cap, device):
-        T = num_tiles(cam)
-        H, W = int(cam.height), int(cam.width)
+    def __init__(self, scene: str, n: int, m_cap: int, max_tiles: int, device):
+        self.scene, self.n, self.m_cap = scene, int(n), int(m_cap)
         self.splats = splat_buffer(n, device)
         self.keys = torch.empty(max(m_cap, 1), dtype=torch.int64, device=device)
         self.vals = torch.empty(max(m_cap, 1), dtype=torch.int32, device=device)
-        self.ranges = torch.empty((T, 2), dtype=torch.int32, device=device)
-        self.workspace = torch.empty(sort_workspace_bytes(n, m_cap, T), dtype=torch.uint8, device=device)
-        self.image = torch.empty((3, H, W), dtype=torch.float32, device=device)
-        self.final_T = torch.empty((H, W), dtype=torch.float32, device=device)
-        self.n_contrib = torch.empty((H, W), dtype=torch.int32, device=device)
-        self.header = torch.empty(4, dtype=torch.int64).pin_memory()   # m_total, nvis|m_sort, overflow|timeout
-        self.m_cap = m_cap
-        self.tiles = T
+        self.ranges = torch.empty((max_tiles, 2), dtype=torch.int32, device=device)
+        self.workspace = torch.empty(sort_workspace_bytes(n, m_cap, max_tiles), dtype=torch.uint8, device=device)
+        self.cam_dev = torch.zeros(CAM_BLOCK_BYTES, dtype=torch.uint8, device=device)
+        self.cam_host = torch.zeros(CAM_BLOCK_BYTES, dtype=torch.uint8).pin_memory()
+        self.header = torch.zeros(4, dtype=torch.int64).pin_memory()  # m_total, nvis|m_sort, overflow|timeout
+        self.stream = torch.cuda.Stream(device)
+        self.graphs = {}  # (width, height) -> captured preprocess + sort
+        self.done_event = None
 
     @staticmethod
-    def bytes_for(n, cam, m_cap) -> int:
-        T = num_tiles(cam)
-        px = int(cam.width) * int(cam.height)
-        return 64 * max(n, 1) + 12 * max(m_cap, 1) + 8 * T + sort_workspace_bytes(n, m_cap, T) + 20 * px
+    def bytes_for(n: int, m_cap: int, max_tiles: int) -> int:
+        return 80 * max(n, 1) + 12 * max(m_cap, 1) + 8 * max_tiles + sort_workspace_bytes(n, m_cap, max_tiles)
+
+    def set_camera(self, cam):
+        c = camera_struct(cam)
+        L.check(L.lib().gs_camera_block(ctypes.byref(c), ctypes.c_void_p(self.cam_host.data_ptr())),
+                "gs_camera_block")
+
+    def front(self, st: SceneTensors, cam, stream):
+        """Preprocess (camera from the slot's camera block) and sort, no host
+        synchronisation; the header of the sort's counters is copied back to
+        pinned memory after it."""
+        with torch.cuda.stream(stream):
+            self.cam_dev.copy_(self.cam_host, non_blocking=True)
+            sc = st.struct()
+            L.check(L.lib().gs_preprocess_camblock(ctypes.byref(sc), _ptr(self.cam_dev), _ptr(self.splats),
+                                                   ctypes.c_void_p(int(stream.cuda_stream))),
+                    "gs_preprocess_camblock")
+            T = num_tiles(cam)
+            sort(self.splats, self.n, cam, self.m_cap, self.keys, self.vals, self.ranges[:T], self.workspace,
+                 count=False, stream=stream)
+            self.header.copy_(self.workspace[:32].view(torch.int64), non_blocking=True)
 
 
 class Server:
-    """scenes: name -> SceneTensors (resident).  m_caps: (scene, width,
-    height) -> instance capacity per request (see ``calibrate``)."""
+    """scenes: name -> SceneTensors (resident).  resolutions: the (width,
+    height) requests may ask for.  ``calibrate`` every (scene, resolution)
+    first; the first ``serve`` call then divides ``mem_budget`` into request
+    slots per scene (at most ``slots_per_scene``, at least one) and captures
+    each slot's preprocess + sort graph per resolution."""
 
-    def __init__(self, scenes: dict, max_batch: int = 16, mem_budget: int = 24 << 30, device="cuda",
-                 n_streams: int = 8, use_graph: bool = True):
+    def __init__(self, scenes: dict, resolutions=None, max_batch: int = 16, mem_budget: int = 24 << 30,
+                 device="cuda", slots_per_scene: int = 8, use_graph: bool = True):
         self.scenes = scenes
+        self.resolutions = [tuple(r) for r in (resolutions or [])]
         self.device = torch.device(device)
         self.max_batch = max_batch
         self.mem_budget = mem_budget
-        self.m_caps = {}
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
-        self.render_stream = torch.cuda.Stream(self.device)
-        cap_desc = DESC_HEADER + JOB_BYTES * max_batch
-        self.desc_host = torch.zeros(cap_desc, dtype=torch.uint8).pin_memory()
-        self.desc_dev = torch.zeros(cap_desc, dtype=torch.uint8, device=self.device)
-        self.counter = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.slots_per_scene = slots_per_scene
         self.use_graph = use_graph
+        self.m_caps = {}
+        self.render_stream = torch.cuda.Stream(self.device)
+        self.batch = RenderBatch(max_batch, device=self.device)
         self.graph = None
+        self.pools = None
         self.stats = collections.Counter()
 
     # ------------------------------------------------------------------ setup
@@ -117,129 +147,153 @@ class Server:
                     cap = max(2 * cap, getattr(e, "m", 0) + 1)
             m = max(m, mm)
         self.m_caps[(scene, width, height)] = int(m * margin) + 4096
+        if (width, height) not in self.resolutions:
+            self.resolutions.append((width, height))
         torch.cuda.synchronize(self.device)
 
-    def _graph_launch(self):
-        lib = L.lib()
-        s = ctypes.c_void_p(int(torch.cuda.current_stream(self.device).cuda_stream))
-        L.check(lib.gs_render_batch(ctypes.c_void_p(self.desc_dev.data_ptr()),
-                                    ctypes.c_void_p(self.counter.data_ptr()), 0, s), "gs_render_batch")
+    def _cam_of(self, w, h):
+        """A placeholder camera of that size for graph capture (the pose
+        comes from the camera block at replay)."""
+        class _C:
+            pass
+        c = _C()
+        c.viewmat = np.eye(4, dtype=np.float32)
+        c.viewmat[2, 3] = 4.0
+        c.fx = c.fy = float(w)
+        c.cx, c.cy = (w - 1) / 2.0, (h - 1) / 2.0
+        c.width, c.height = int(w), int(h)
+        c.tan_fovx, c.tan_fovy = 0.5, 0.5 * h / w
+        return c
 
-    def _ensure_graph(self):
-        if self.graph is not None or not self.use_graph:
+    def _ensure_ready(self):
+        if self.pools is not None:
             return
-        # an empty batch, then capture the launch (memset + persistent kernel)
-        self.desc_host.zero_()
-        self.desc_dev.copy_(self.desc_host)
+        max_tiles = max(num_tiles(self._cam_of(w, h)) for w, h in self.resolutions)
+        per_scene = self.mem_budget // max(1, len(self.scenes))
+        self.pools = {}
+        for name, st in self.scenes.items():
+            m_cap = max(v for (s, _, _), v in self.m_caps.items() if s == name)
+            nbytes = _Slot.bytes_for(st.n, m_cap, max_tiles)
+            count = max(1, min(self.slots_per_scene, per_scene // nbytes))
+            self.pools[name] = [_Slot(name, st.n, m_cap, max_tiles, self.device) for _ in range(count)]
+            self.stats[f"slots_{name}"] = count
         torch.cuda.synchronize(self.device)
+        # warm-up outside capture (first calls look up device attributes)
+        for name, pool in self.pools.items():
+            for w, h in self.resolutions:
+                cam = self._cam_of(w, h)
+                pool[0].set_camera(cam)
+                pool[0].front(self.scenes[name], cam, pool[0].stream)
+        self.batch.set_jobs([], stream=self.render_stream)
         with torch.cuda.stream(self.render_stream):
-            self._graph_launch()  # warm-up outside the capture
+            self.batch.launch(stream=self.render_stream)
         torch.cuda.synchronize(self.device)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=self.render_stream):
-            self._graph_launch()
-        self.graph = g
+        if self.use_graph:
+            for name, pool in self.pools.items():
+                st = self.scenes[name]
+                for slot in pool:
+                    for w, h in self.resolutions:
+                        g = torch.cuda.CUDAGraph()
+                        cam = self._cam_of(w, h)
+                        with torch.cuda.graph(g, stream=slot.stream):
+                            slot.front(st, cam, slot.stream)
+                        slot.graphs[(w, h)] = g
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.render_stream):
+                self.batch.upload(stream=self.render_stream)
+                self.batch.launch(stream=self.render_stream)
+            self.graph = g
         torch.cuda.synchronize(self.device)
 
     # -------------------------------------------------------------- requests
-    def _admit(self, req: Request, stream: torch.cuda.Stream):
-        st = self.scenes[req.scene]
-        key = (req.scene, int(req.cam.width), int(req.cam.height))
-        m_cap = self.m_caps[key]
-        with torch.cuda.stream(stream):
-            slot = _Slot(st.n, req.cam, m_cap, self.device)
-            preprocess(st, req.cam, slot.splats, stream=stream)
-            sort(slot.splats, st.n, req.cam, m_cap, slot.keys, slot.vals, slot.ranges, slot.workspace, count=False,
-                 stream=stream)
-            slot.header.copy_(slot.workspace[:32].view(torch.int64), non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        return slot, ev
+    def _front(self, req: Request, slot: _Slot):
+        slot.set_camera(req.cam)
+        key = (int(req.cam.width), int(req.cam.height))
+        if self.use_graph:
+            with torch.cuda.stream(slot.stream):
+                slot.graphs[key].replay()
+        else:
+            slot.front(self.scenes[req.scene], req.cam, slot.stream)
+        ev = torch.cuda.Event()
+        ev.record(slot.stream)
+        return ev
 
-    def _write_desc(self, batch):
-        host = self.desc_host.numpy()
-        total = 0
-        jobs = np.zeros(len(batch), dtype=np.dtype([("splats", "<u8"), ("vals", "<u8"), ("ranges", "<u8"),
-                                                    ("out", "<u8"), ("T", "<u8"), ("nc", "<u8"), ("w", "<i4"),
-                                                    ("h", "<i4"), ("bg", "<f4", 3), ("tile_begin", "<u4")]))
-        for i, (req, slot) in enumerate(batch):
-            jobs[i] = (slot.splats.data_ptr(), slot.vals.data_ptr(), slot.ranges.data_ptr(), slot.image.data_ptr(),
-                       slot.final_T.data_ptr(), slot.n_contrib.data_ptr(), int(req.cam.width), int(req.cam.height),
-                       req.bg, total)
-            total += slot.tiles
-        assert jobs.dtype.itemsize == JOB_BYTES
-        hdr = np.zeros(DESC_HEADER, np.uint8)
-        hdr[:8] = np.frombuffer(np.array([len(batch), total], dtype=np.uint32).tobytes(), np.uint8)
-        host[:DESC_HEADER] = hdr
-        host[DESC_HEADER:DESC_HEADER + JOB_BYTES * len(batch)] = np.frombuffer(jobs.tobytes(), np.uint8)
-        return total
+    def _outputs(self, req: Request):
+        H, W = int(req.cam.height), int(req.cam.width)
+        dev = self.device
+        return (torch.empty((3, H, W), dtype=torch.float32, device=dev),
+                torch.empty((H, W), dtype=torch.float32, device=dev),
+                torch.empty((H, W), dtype=torch.int32, device=dev))
+
+    def _finish(self, req: Request, slot: _Slot, t_done: float, done: list):
+        req.t_done = t_done
+        req.instances = int(slot.header[0])
+        flags = int(slot.header[2])  # overflow | timeout << 32
+        if flags & 0xFFFFFFFF:
+            req.error = "capacity"
+        elif flags >> 32:
+            req.error = "timeout"
+        if req.error:
+            req.image = req.final_T = req.n_contrib = None
+            self.stats["failed"] += 1
+        done.append(req)
 
     def serve(self, requests: list[Request], realtime: bool = True):
         """Serves the requests (sorted by arrival).  With realtime=False all
         requests are present at t = 0 (a saturation run)."""
-        self._ensure_graph()
+        self._ensure_ready()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        free = {name: list(pool) for name, pool in self.pools.items()}
         prepared = []             # (req, slot, event)
         rendering = None          # (batch, event)
-        mem_used = 0
-        sidx = 0
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
         done = []
         while pending or prepared or rendering:
             t = now()
-            # admission: arrived requests while a slot and memory are free
-            while pending and (not realtime or pending[0].arrival <= t) and \
-                    len(prepared) + (len(rendering[0]) if rendering else 0) < 2 * self.max_batch:
+            # admission: arrived requests while a slot of their scene is free
+            while pending and (not realtime or pending[0].arrival <= t):
                 req = pending[0]
-                key = (req.scene, int(req.cam.width), int(req.cam.height))
-                need = _Slot.bytes_for(self.scenes[req.scene].n, req.cam, self.m_caps[key])
-                if mem_used + need > self.mem_budget and (prepared or rendering):
+                if not free[req.scene]:
                     self.stats["admission_waits"] += 1
                     break
                 pending.popleft()
+                slot = free[req.scene].pop()
                 req.t_admit = now()
-                slot, ev = self._admit(req, self.streams[sidx % len(self.streams)])
-                sidx += 1
-                mem_used += need
-                prepared.append((req, slot, ev, need))
+                prepared.append((req, slot, self._front(req, slot)))
             # completion of the batch in flight
             if rendering and rendering[1].query():
                 tdone = now()
-                for req, slot, _, need in rendering[0]:
-                    req.t_done = tdone
-                    req.image, req.final_T, req.n_contrib = slot.image, slot.final_T, slot.n_contrib
-                    req.instances = int(slot.header[0])
-                    if int(slot.header[2]) != 0:  # overflow | timeout << 32
-                        self.stats["overflow_or_timeout"] += 1
-                    mem_used -= need
-                    done.append(req)
+                for req, slot, _ in rendering[0]:
+                    self._finish(req, slot, tdone, done)
+                    free[slot.scene].append(slot)
                 self.stats["batches"] += 1
                 rendering = None
             # launch a batch of the prepared requests as soon as the render
             # engine is free: the render stream waits for their sorts on the
             # device, so no host round trip sits between a sort and its render
             if rendering is None and prepared:
-                ready = prepared
-                if ready:
-                    batch = ready[: self.max_batch]
-                    for b in batch:
-                        prepared.remove(b)
-                    total = self._write_desc([(r, s) for r, s, _, _ in batch])
-                    rs = self.render_stream
-                    for _, _, ev, _ in batch:
-                        rs.wait_event(ev)
-                    with torch.cuda.stream(rs):
-                        self.desc_dev.copy_(self.desc_host, non_blocking=True)
-                        if self.graph is not None:
-                            self.graph.replay()
-                        else:
-                            self._graph_launch()
-                        ev = torch.cuda.Event()
-                        ev.record(rs)
-                    self.stats["jobs"] += len(batch)
-                    self.stats["tiles"] += total
-                    rendering = (batch, ev)
+                batch, prepared = prepared[: self.max_batch], prepared[self.max_batch:]
+                jobs = []
+                for req, slot, _ in batch:
+                    req.image, req.final_T, req.n_contrib = self._outputs(req)
+                    jobs.append(BatchJob(slot.splats, slot.vals, slot.ranges, req.image, req.final_T, req.n_contrib,
+                                         req.cam.width, req.cam.height, req.bg))
+                total = self.batch.write(jobs)
+                rs = self.render_stream
+                for _, _, ev in batch:
+                    rs.wait_event(ev)
+                with torch.cuda.stream(rs):
+                    if self.graph is not None:
+                        self.graph.replay()
+                    else:
+                        self.batch.upload(stream=rs)
+                        self.batch.launch(stream=rs)
+                    ev = torch.cuda.Event()
+                    ev.record(rs)
+                self.stats["jobs"] += len(batch)
+                self.stats["tiles"] += total
+                rendering = (batch, ev)
             if not (rendering or prepared) and pending and realtime:
                 wait = pending[0].arrival - now()
                 if wait > 0:
@@ -249,30 +303,27 @@ class Server:
         return done, wall
 
     def serve_sequential(self, requests: list[Request], realtime: bool = True):
-        """One request at a time: preprocess, sort, render, wait; FIFO."""
+        """One request at a time, FIFO, on the same slots and captured
+        preprocess + sort: front, gs_render, wait."""
+        self._ensure_ready()
         order = sorted(requests, key=lambda r: r.arrival)
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
-        stream = self.streams[0]
+        done = []
         for req in order:
             if realtime:
                 wait = req.arrival - now()
                 if wait > 0:
                     time.sleep(wait)
             req.t_admit = now()
-            st = self.scenes[req.scene]
-            key = (req.scene, int(req.cam.width), int(req.cam.height))
-            with torch.cuda.stream(stream):
-                slot = _Slot(st.n, req.cam, self.m_caps[key], self.device)
-                preprocess(st, req.cam, slot.splats, stream=stream)
-                sort(slot.splats, st.n, req.cam, slot.m_cap, slot.keys, slot.vals, slot.ranges, slot.workspace,
-                     count=False, stream=stream)
-                render(slot.splats, slot.vals, slot.ranges, req.cam, req.bg, slot.image, slot.final_T,
-                       slot.n_contrib, stream=stream)
-            stream.synchronize()
-            req.t_done = now()
-            req.image, req.final_T, req.n_contrib = slot.image, slot.final_T, slot.n_contrib
-        return order, now()
+            slot = self.pools[req.scene][0]
+            self._front(req, slot)
+            req.image, req.final_T, req.n_contrib = self._outputs(req)
+            render(slot.splats, slot.vals, slot.ranges[:num_tiles(req.cam)], req.cam, req.bg, req.image,
+                   req.final_T, req.n_contrib, stream=slot.stream)
+            slot.stream.synchronize()
+            self._finish(req, slot, now(), done)
+        return done, now()
 
 
 def poisson_requests(rate: float, duration: float, scenes: list[str], resolutions: list[tuple], cam_fn, seed: int = 0):
@@ -290,6 +341,10 @@ def poisson_requests(rate: float, duration: float, scenes: list[str], resolution
 
 
 def latency_stats(done: list[Request], wall: float) -> dict:
-    lat = np.array([r.latency for r in done]) * 1000.0
-    return dict(requests=len(done), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                mean_ms=float(lat.mean()), frames_per_s=len(done) / wall, wall_s=wall)
+    """Latency percentiles and throughput of the completed requests (failed
+    ones are counted apart)."""
+    ok = [r for r in done if r.error is None]
+    lat = np.array([r.latency for r in ok]) * 1000.0 if ok else np.array([math.nan])
+    return dict(requests=len(ok), failed=len(done) - len(ok), p50_ms=float(np.percentile(lat, 50)),
+                p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), frames_per_s=len(ok) / wall,
+                wall_s=wall)

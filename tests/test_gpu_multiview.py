@@ -2,15 +2,11 @@
 each view's outputs equal its own gs_render bit for bit, on a slab scene
 whose occluding slab makes a few tiles far heavier than the rest."""
 
-import ctypes
-
 import numpy as np
 import pytest
 import torch
 
 import paper_2509_25626_gb300 as gs
-from paper_2509_25626_gb300 import _lib as L
-from paper_2509_25626_gb300 import serve as S
 from synth import orbit_camera, slab_scene
 
 pytestmark = pytest.mark.gpu
@@ -28,24 +24,9 @@ def test_multiview_batch_equals_single_views():
     lens = [int((r[:, 1] - r[:, 0]).max()) for _, _, _, r, _ in views]
     assert max(lens) > 20 * np.mean([float((r[:, 1] - r[:, 0]).float().mean()) for _, _, _, r, _ in views])
     outs = [tuple(torch.empty_like(t) for t in v[4]) for v in views]
-    srv = S.Server({}, max_batch=8)
-
-    class _Req:
-        def __init__(self, cam):
-            self.cam, self.bg = cam, (0.0, 0.0, 0.0)
-
-    class _Slot:
-        def __init__(self, sp, vals, ranges, out, cam):
-            self.splats, self.vals, self.ranges = sp, vals, ranges
-            self.image, self.final_T, self.n_contrib = out
-            self.tiles = gs.num_tiles(cam)
-
-    batch = [(_Req(c), _Slot(sp, v, r, o, c)) for (c, sp, v, r, _), o in zip(views, outs)]
-    srv._write_desc(batch)
-    srv.desc_dev.copy_(srv.desc_host)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
-                                    ctypes.c_void_p(srv.counter.data_ptr()), 0, stream), "gs_render_batch")
+    rb = gs.RenderBatch(8)
+    rb.set_jobs([gs.BatchJob(sp, v, r, *o, c.width, c.height) for (c, sp, v, r, _), o in zip(views, outs)])
+    rb.launch()
     torch.cuda.synchronize()
     for (cam, sp, vals, ranges, ref), out in zip(views, outs):
         for a, b in zip(out, ref):
@@ -69,23 +50,9 @@ def test_batch_job_table_sizes(n_jobs):
         _, vals, ranges, m, _ = gs.sort(sp, st.n, cam, 1 << 20)
         ref = gs.render(sp, vals, ranges, cam, bg)
         jobs.append((cam, bg, sp, vals, ranges, ref, tuple(torch.empty_like(t) for t in ref)))
-    srv = S.Server({}, max_batch=n_jobs)
-
-    class _Req:
-        def __init__(self, cam, bg):
-            self.cam, self.bg = cam, bg
-
-    class _Slot:
-        def __init__(self, sp, vals, ranges, out, cam):
-            self.splats, self.vals, self.ranges = sp, vals, ranges
-            self.image, self.final_T, self.n_contrib = out
-            self.tiles = gs.num_tiles(cam)
-
-    srv._write_desc([(_Req(c, bg), _Slot(sp, v, r, o, c)) for c, bg, sp, v, r, _, o in jobs])
-    srv.desc_dev.copy_(srv.desc_host)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
-                                    ctypes.c_void_p(srv.counter.data_ptr()), 0, stream), "gs_render_batch")
+    rb = gs.RenderBatch(n_jobs)
+    rb.set_jobs([gs.BatchJob(sp, v, r, *o, c.width, c.height, bg) for c, bg, sp, v, r, _, o in jobs])
+    rb.launch()
     torch.cuda.synchronize()
     for c, bg, sp, v, r, ref, out in jobs:
         for a, b in zip(out, ref):
@@ -115,23 +82,10 @@ def test_full_size_slab_views_sampled(oracle):
         assert not over
         rs.append((r, m))
     outs = [tuple(torch.empty_like(t) for t in (r.image, r.final_T, r.n_contrib)) for r, _ in rs]
-    srv = S.Server({}, max_batch=2)
-
-    class _Req:
-        def __init__(self, cam):
-            self.cam, self.bg = cam, (0.0, 0.0, 0.0)
-
-    class _Slot:
-        def __init__(self, r, out, cam):
-            self.splats, self.vals, self.ranges = r.splats, r.vals, r.ranges
-            self.image, self.final_T, self.n_contrib = out
-            self.tiles = gs.num_tiles(cam)
-
-    srv._write_desc([(_Req(c), _Slot(r, o, c)) for c, (r, _), o in zip(cams, rs, outs)])
-    srv.desc_dev.copy_(srv.desc_host)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L.check(L.lib().gs_render_batch(ctypes.c_void_p(srv.desc_dev.data_ptr()),
-                                    ctypes.c_void_p(srv.counter.data_ptr()), 0, stream), "gs_render_batch")
+    rb = gs.RenderBatch(2)
+    rb.set_jobs([gs.BatchJob(r.splats, r.vals, r.ranges, *o, c.width, c.height) for c, (r, _), o in
+                 zip(cams, rs, outs)])
+    rb.launch()
     torch.cuda.synchronize()
     for (r, _), out in zip(rs, outs):
         for a, b in zip(out, (r.image, r.final_T, r.n_contrib)):

@@ -108,9 +108,13 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int width, int height) {
 // Returns the first entry not walked (`to` if the walk reached the end or
 // every pixel is done).  Every thread must call it; it begins each round
 // with a block-wide barrier.
-template <bool kDepth>
-__device__ __forceinline__ uint32_t walk_tile(RenderSmem &sm, const gs_splat *__restrict__ splats,
-                                              const uint32_t *__restrict__ vals, uint32_t begin, uint32_t from,
+// The job's splat and value pointers are read where a round stages its
+// batch, not held in registers across the walk: the batch kernels keep the
+// job in shared memory, the single-image kernel in its parameters.
+// kBudget: max_rounds is honoured (the split render's budgeted walk); the
+// other walks compile without the round count.
+template <bool kDepth, bool kBudget = false>
+__device__ __forceinline__ uint32_t walk_tile(RenderSmem &sm, const gs_render_job &job, uint32_t begin, uint32_t from,
                                               uint32_t to, uint32_t max_rounds, const TileGeom &g, Pixel &p0,
                                               Pixel &p1) {
     StagedA *s_a = sm.a;
@@ -126,7 +130,9 @@ __device__ __forceinline__ uint32_t walk_tile(RenderSmem &sm, const gs_splat *__
     for (; base < to; base += kBatch) {
         // every thread has finished the previous round; stop if all pixels are done
         if (__syncthreads_and(p0.done && p1.done)) return to;
-        if (rounds++ == max_rounds) return base;  // uniform: every thread counts the same rounds
+        if (kBudget && rounds++ == max_rounds) return base;  // uniform: every thread counts the same rounds
+        const gs_splat *__restrict__ splats = job.splats;
+        const uint32_t *__restrict__ vals = job.vals;
 #pragma unroll
         for (int r = 0; r < kBatch / kThreads; ++r) {
             const int k = (int)threadIdx.x + r * kThreads;
@@ -239,7 +245,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
     const TileGeom g = tile_geom(tile, job.width, job.height);
     Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in0};
     Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in1};
-    walk_tile<kDepth>(sm, job.splats, job.vals, range.x, range.x, range.y, 0xffffffffu, g, p0, p1);
+    walk_tile<kDepth>(sm, job, range.x, range.x, range.y, 0xffffffffu, g, p0, p1);
     store_tile<kCount, kDepth>(job, g, p0, p1, range.y - range.x, invdepth, n_eval);
     if (kCount && tile_cycles != nullptr && threadIdx.x == 0) {
         const long long dt = clock64() - t_start;
@@ -390,81 +396,89 @@ __global__ void __launch_bounds__(256) classify_kernel(const gs_render_batch_des
 // kHeavy: the items classify_kernel queued come first (item i < n_heavy
 // is queued tile heavy[i]), then every tile in order, skipping the queued
 // ones; if the queue overflowed it is ignored and the order is the plain one.
+#ifndef GS_BATCH_MIN_BLOCKS
+#define GS_BATCH_MIN_BLOCKS 10
+#endif
 template <bool kSplit, bool kHeavy>
-__global__ void __launch_bounds__(kThreads, 10) render_batch_kernel(const gs_render_batch_desc *__restrict__ desc,
-                                                                uint32_t *__restrict__ counter, SplitLayout sl,
-                                                                uint32_t budget_rounds) {
+__global__ void __launch_bounds__(kThreads, GS_BATCH_MIN_BLOCKS) render_batch_kernel(
+    const gs_render_batch_desc *__restrict__ desc, uint32_t *__restrict__ counter, SplitLayout sl,
+    uint32_t budget_rounds) {
     constexpr int kJobWords = (int)(sizeof(gs_render_job) / 4);
     static_assert(sizeof(gs_render_job) % 4 == 0 && kJobWords <= kThreads, "job copy");
     __shared__ RenderSmem sm;
     __shared__ gs_render_job s_jobs[kJobsCached];
-    __shared__ uint32_t s_w, s_slot;
-    const int n_jobs = desc->n_jobs;
-    uint32_t nh = 0;
-    if (kHeavy) {
-        nh = *sl.n_heavy;
-        if (nh > sl.heavy_cap) nh = 0;
+    // the loop's state lives here, not in registers across the tile walk
+    __shared__ uint32_t s_w, s_next, s_slot, s_nh, s_total;
+    __shared__ int s_njobs;
+    if (threadIdx.x == 0) {
+        uint32_t nh = 0;
+        if (kHeavy) {
+            nh = *sl.n_heavy;
+            if (nh > sl.heavy_cap) nh = 0;
+        }
+        s_nh = nh;
+        s_total = desc->total_tiles + nh;
+        s_njobs = desc->n_jobs;
+        s_w = atomicAdd(counter, 1u);
     }
-    const uint32_t total = desc->total_tiles + nh;
-    const bool cached = cache_jobs(s_jobs, desc, n_jobs);
-    if (threadIdx.x == 0) s_w = atomicAdd(counter, 1u);
+    cache_jobs(s_jobs, desc, desc->n_jobs);
     __syncthreads();
-    for (uint32_t item = s_w; item < total;) {
-        uint32_t next = 0;
-        if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
+    for (;;) {
+        const uint32_t item = s_w;
+        if (item >= s_total) break;  // uniform
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);  // read after this tile
+        const int n_jobs = s_njobs;
+        const bool cached = n_jobs <= kJobsCached;
+        const uint32_t nh = kHeavy ? s_nh : 0u;
         const uint32_t w = (kHeavy && item < nh) ? __ldg(sl.heavy + item) : item - nh;
         int lo = job_of(s_jobs, cached, desc, n_jobs, w);
-        if (kHeavy && nh > 0 && item >= nh &&
-            list_length(cached ? s_jobs[lo] : desc->jobs[lo], w) >= sl.heavy_len) {
-            // queued and rendered first: skip (uniform)
-            if (threadIdx.x == 0) s_w = next;
-            __syncthreads();
-            item = s_w;
-            __syncthreads();
-            continue;
-        }
-        const uint32_t jidx = (uint32_t)lo;
-        if (!cached) {
-            // the previous tile ended with a barrier, so slot 0 is free
-            fetch_job(&s_jobs[0], desc, jidx);
-            __syncthreads();
-            lo = 0;
-        }
-        const gs_render_job &job = s_jobs[lo];
-        const int tile = (int)(w - job.tile_begin);
-        const uint2 range = reinterpret_cast<const uint2 *>(job.ranges)[tile];
-        if (!kSplit) {
-            render_tile<false, false>(sm, job, range, tile, nullptr, nullptr, nullptr);
-        } else {
-            const TileGeom g = tile_geom(tile, job.width, job.height);
-            Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in0};
-            Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in1};
-            uint32_t at = walk_tile<false>(sm, job.splats, job.vals, range.x, range.x, range.y, budget_rounds, g, p0,
-                                           p1);
-            bool queued = false;
-            if (at < range.y) {  // uniform: the budget ran out with live pixels
-                if (threadIdx.x == 0) s_slot = atomicAdd(sl.n_entries, 1u);
+        const bool skip = kHeavy && nh > 0 && item >= nh &&
+                          list_length(cached ? s_jobs[lo] : desc->jobs[lo], w) >= sl.heavy_len;
+        if (!skip) {  // uniform; a skipped item was queued and rendered first
+            const uint32_t jidx = (uint32_t)lo;
+            if (!cached) {
+                // the previous tile ended with a barrier, so slot 0 is free
+                fetch_job(&s_jobs[0], desc, jidx);
                 __syncthreads();
-                const uint32_t slot = s_slot;
-                if (slot < sl.cap) {
-                    queued = true;
-                    if (threadIdx.x == 0) sl.entries[slot] = SplitEntry{jidx, (uint32_t)tile, range.x, at, range.y, {0u, 0u, 0u}};
-                    const size_t px = (size_t)slot * kTilePixels + 2 * threadIdx.x;
-                    pixel_save(sl.state + px, sl.state_last + px, p0, p0.done);
-                    pixel_save(sl.state + px + 1, sl.state_last + px + 1, p1, p1.done);
-                } else {
-                    walk_tile<false>(sm, job.splats, job.vals, range.x, at, range.y, 0xffffffffu, g, p0, p1);
-                }
+                lo = 0;
             }
-            if (!queued)
-                store_tile<false, false>(job, g, p0, p1, 0u, nullptr, nullptr);
-            else
-                __syncthreads();  // as store_tile: shared memory free for the next tile
+            const gs_render_job &job = s_jobs[lo];
+            const int tile = (int)(w - job.tile_begin);
+            const uint2 range = reinterpret_cast<const uint2 *>(job.ranges)[tile];
+            if (!kSplit) {
+                render_tile<false, false>(sm, job, range, tile, nullptr, nullptr, nullptr);
+            } else {
+                const TileGeom g = tile_geom(tile, job.width, job.height);
+                Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in0};
+                Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in1};
+                uint32_t at = walk_tile<false, true>(sm, job, range.x, range.x, range.y, budget_rounds, g, p0, p1);
+                bool queued = false;
+                if (at < range.y) {  // uniform: the budget ran out with live pixels
+                    if (threadIdx.x == 0) s_slot = atomicAdd(sl.n_entries, 1u);
+                    __syncthreads();
+                    const uint32_t slot = s_slot;
+                    if (slot < sl.cap) {
+                        queued = true;
+                        if (threadIdx.x == 0)
+                            sl.entries[slot] = SplitEntry{jidx, (uint32_t)tile, range.x, at, range.y, {0u, 0u, 0u}};
+                        const size_t px = (size_t)slot * kTilePixels + 2 * threadIdx.x;
+                        pixel_save(sl.state + px, sl.state_last + px, p0, p0.done);
+                        pixel_save(sl.state + px + 1, sl.state_last + px + 1, p1, p1.done);
+                    } else {
+                        walk_tile<false>(sm, job, range.x, at, range.y, 0xffffffffu, g, p0, p1);
+                    }
+                }
+                if (!queued)
+                    store_tile<false, false>(job, g, p0, p1, 0u, nullptr, nullptr);
+                else
+                    __syncthreads();  // as store_tile: shared memory free for the next tile
+            }
+        } else {
+            __syncthreads();  // s_next is written before it is read
         }
         // the tile ended with a barrier: nobody reads s_w any more
-        if (threadIdx.x == 0) s_w = next;
+        if (threadIdx.x == 0) s_w = s_next;
         __syncthreads();
-        item = s_w;
     }
 }
 
@@ -498,8 +512,7 @@ __global__ void __launch_bounds__(kThreads, 10) split_chunk_kernel(const gs_rend
             const TileGeom g = tile_geom((int)ent.tile, s_job.width, s_job.height);
             Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in0};
             Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in1};
-            walk_tile<false>(sm, s_job.splats, s_job.vals, ent.begin, s0, min(ent.end, s0 + csz), 0xffffffffu, g,
-                             p0, p1);
+            walk_tile<false>(sm, s_job, ent.begin, s0, min(ent.end, s0 + csz), 0xffffffffu, g, p0, p1);
             const size_t px = ((size_t)e * sl.K + c) * kTilePixels + 2 * threadIdx.x;
             pixel_save(sl.part + px, sl.part_last + px, p0, p0.stop != 0u);
             pixel_save(sl.part + px + 1, sl.part_last + px + 1, p1, p1.stop != 0u);
@@ -559,8 +572,7 @@ __global__ void __launch_bounds__(kThreads, 10) split_merge_kernel(const gs_rend
                 const bool hold0 = !p0.done && !x0, hold1 = !p1.done && !x1;
                 if (hold0) p0.done = true;
                 if (hold1) p1.done = true;
-                walk_tile<false>(sm, s_job.splats, s_job.vals, ent.begin, s0, min(ent.end, s0 + csz), 0xffffffffu,
-                                 g, p0, p1);
+                walk_tile<false>(sm, s_job, ent.begin, s0, min(ent.end, s0 + csz), 0xffffffffu, g, p0, p1);
                 if (hold0) p0.done = false;
                 if (hold1) p1.done = false;
             }
@@ -568,8 +580,7 @@ __global__ void __launch_bounds__(kThreads, 10) split_merge_kernel(const gs_rend
         // the list beyond the chunked window, from the merged state (exact)
         const uint64_t window_end = (uint64_t)ent.pos + (uint64_t)sl.K * csz;
         if (window_end < ent.end)
-            walk_tile<false>(sm, s_job.splats, s_job.vals, ent.begin, (uint32_t)window_end, ent.end, 0xffffffffu, g,
-                             p0, p1);
+            walk_tile<false>(sm, s_job, ent.begin, (uint32_t)window_end, ent.end, 0xffffffffu, g, p0, p1);
         store_tile<false, false>(s_job, g, p0, p1, 0u, nullptr, nullptr);
     }
 }

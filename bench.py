@@ -673,12 +673,13 @@ def measure_serving(gs, dev, rates=(200.0, 800.0, 1600.0, 2400.0), duration: flo
     out = {"rates": {}}
     for rate in rates:
         row = {}
+        dur = max(duration, 500.0 / rate)  # at least ~500 requests per rate, so that p99 is not the maximum
         for mode in ("batched", "sequential"):
-            reqs = S.poisson_requests(rate, duration, list(scenes), res, cam_fn, seed=99)
+            reqs = S.poisson_requests(rate, dur, list(scenes), res, cam_fn, seed=99)
             fn = srv.serve if mode == "batched" else srv.serve_sequential
             done, wall = fn(reqs, realtime=True)
             row[mode] = S.latency_stats(done, wall)
-            row[mode]["offered_per_s"] = len(reqs) / duration
+            row[mode]["offered_per_s"] = len(reqs) / dur
         out["rates"][f"{int(rate)}"] = row
     for mode in ("batched", "sequential"):
         sat = S.poisson_requests(rates[-1], duration, list(scenes), res, cam_fn, seed=100)

@@ -113,7 +113,8 @@ class Server:
     each slot's preprocess + sort graph per resolution."""
 
     def __init__(self, scenes: dict, resolutions=None, max_batch: int = 16, mem_budget: int = 24 << 30,
-                 device="cuda", slots_per_scene: int = 8, use_graph: bool = True):
+                 device="cuda", slots_per_scene: int = 8, use_graph: bool = True, render_priority: bool = False,
+                 single_direct: bool = True):
         self.scenes = scenes
         self.resolutions = [tuple(r) for r in (resolutions or [])]
         self.device = torch.device(device)
@@ -121,8 +122,12 @@ class Server:
         self.mem_budget = mem_budget
         self.slots_per_scene = slots_per_scene
         self.use_graph = use_graph
+        self.single_direct = single_direct
         self.m_caps = {}
-        self.render_stream = torch.cuda.Stream(self.device)
+        # render_priority: the batch render at the highest stream priority
+        # (measured no better for latency at 200 and 800 requests/s)
+        prio = torch.cuda.Stream.priority_range()[1] if render_priority else 0
+        self.render_stream = torch.cuda.Stream(self.device, priority=prio)
         self.batch = RenderBatch(max_batch, device=self.device)
         self.graph = None
         self.pools = None
@@ -279,16 +284,28 @@ class Server:
                     req.image, req.final_T, req.n_contrib = self._outputs(req)
                     jobs.append(BatchJob(slot.splats, slot.vals, slot.ranges, req.image, req.final_T, req.n_contrib,
                                          req.cam.width, req.cam.height, req.bg))
-                total = self.batch.write(jobs)
                 rs = self.render_stream
-                for _, _, ev in batch:
-                    rs.wait_event(ev)
+                if len(batch) == 1 and self.single_direct:
+                    # a batch of one: gs_render itself (the same blend, bit
+                    # for bit), on the request's own stream right after its
+                    # sort -- no job table, no cross-stream wait
+                    req, slot, _ = batch[0]
+                    rs = slot.stream
+                else:
+                    for _, _, ev in batch:
+                        rs.wait_event(ev)
                 with torch.cuda.stream(rs):
-                    if self.graph is not None:
-                        self.graph.replay()
+                    if len(batch) == 1 and self.single_direct:
+                        render(slot.splats, slot.vals, slot.ranges[:num_tiles(req.cam)], req.cam, req.bg, req.image,
+                               req.final_T, req.n_contrib, stream=rs)
+                        total = num_tiles(req.cam)
                     else:
-                        self.batch.upload(stream=rs)
-                        self.batch.launch(stream=rs)
+                        total = self.batch.write(jobs)
+                        if self.graph is not None:
+                            self.graph.replay()
+                        else:
+                            self.batch.upload(stream=rs)
+                            self.batch.launch(stream=rs)
                     ev = torch.cuda.Event()
                     ev.record(rs)
                 self.stats["jobs"] += len(batch)

@@ -247,10 +247,15 @@ constexpr int kShStride = 49;  // 48 floats + 1: rows start in different banks
 __device__ __forceinline__ void preprocess_backward_one(
     const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
     const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
-    const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
+    uint32_t tiles, const float *__restrict__ dsplat, float *__restrict__ dmeans,
     float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits);
 
-__global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
+#ifdef GS_PREBACK_MIN_BLOCKS
+#define GS_PREBACK_BOUNDS __launch_bounds__(kPreBackThreads, GS_PREBACK_MIN_BLOCKS)
+#else
+#define GS_PREBACK_BOUNDS __launch_bounds__(kPreBackThreads)
+#endif
+__global__ void GS_PREBACK_BOUNDS preprocess_backward_kernel(
     const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
     const float *__restrict__ logits, const float *__restrict__ sh, int64_t n, int sh_degree, CamParams cam,
     const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
@@ -260,8 +265,15 @@ __global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
     // global loads and stores are coalesced (one thread's 48 floats span 192
     // bytes); a thread reads its own row and overwrites it with its gradient.
     __shared__ float s_sh[kPreBackThreads][kShStride];
+    __shared__ uint32_t s_tiles[kPreBackThreads];
     const int64_t g0 = (int64_t)blockIdx.x * kPreBackThreads;
     const int nb = (int)min((int64_t)kPreBackThreads, n - g0);  // Gaussians of this block
+    // visibility first, from the dense copy of the sort inputs (16 bytes per
+    // Gaussian, not a word of each 64-byte record): a culled Gaussian's SH
+    // coefficients are never read (its gradients are zeros)
+    const uint4 *sort_in = reinterpret_cast<const uint4 *>(splats + n);
+    if ((int)threadIdx.x < nb) s_tiles[threadIdx.x] = __ldg(&sort_in[g0 + threadIdx.x].y);
+    __syncthreads();
     // full blocks with 16-byte aligned SH arrays move them as float4, all 12
     // loads of a thread in flight at once
     const bool vec = nb == kPreBackThreads &&
@@ -270,7 +282,10 @@ __global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
         const float4 *src = reinterpret_cast<const float4 *>(sh + g0 * 48);
         float4 v[12];
 #pragma unroll
-        for (int r = 0; r < 12; ++r) v[r] = __ldg(src + threadIdx.x + r * kPreBackThreads);
+        for (int r = 0; r < 12; ++r) {
+            const int f4 = (int)threadIdx.x + r * kPreBackThreads;
+            v[r] = s_tiles[(4 * f4) / 48] ? __ldg(src + f4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
         for (int r = 0; r < 12; ++r) {
             const int f = 4 * ((int)threadIdx.x + r * kPreBackThreads), row = f / 48, col = f % 48;
@@ -280,12 +295,13 @@ __global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
             s_sh[row][col + 3] = v[r].w;
         }
     } else {
-        for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads) s_sh[f / 48][f % 48] = sh[g0 * 48 + f];
+        for (int f = threadIdx.x; f < nb * 48; f += kPreBackThreads)
+            s_sh[f / 48][f % 48] = s_tiles[f / 48] ? sh[g0 * 48 + f] : 0.f;
     }
     __syncthreads();
     const int64_t gi = g0 + threadIdx.x;
     if (gi < n) preprocess_backward_one(means, log_scales, quats, logits, s_sh[threadIdx.x], gi, sh_degree, cam,
-                                        splats, dsplat, dmeans, dlog_scales, dquats, dlogits);
+                                        s_tiles[threadIdx.x], dsplat, dmeans, dlog_scales, dquats, dlogits);
     __syncthreads();
     if (vec) {
         float4 *dst = reinterpret_cast<float4 *>(dsh + g0 * 48);
@@ -299,14 +315,56 @@ __global__ void __launch_bounds__(kPreBackThreads) preprocess_backward_kernel(
     }
 }
 
+// The real SH basis function k (degree <= 3, Condon-Shortley phase, k =
+// l^2 + l + m) at the unit direction (x, y, z), and its gradient with
+// respect to the direction, in Cartesian form; xx, yy, zz are the squares.
+// k is a constant after unrolling, so only one branch survives (the basis
+// values are not kept in arrays, which put them in local memory).
+__device__ __forceinline__ void sh_term(int k, float x, float y, float z, float xx, float yy, float zz, float &Y,
+                                        float &gx, float &gy, float &gz) {
+    gx = gy = gz = 0.f;
+    switch (k) {
+        case 0: Y = kSH0; break;
+        case 1: Y = -kSH1 * y; gy = -kSH1; break;
+        case 2: Y = kSH1 * z; gz = kSH1; break;
+        case 3: Y = -kSH1 * x; gx = -kSH1; break;
+        case 4: Y = kSH2a * x * y; gx = kSH2a * y; gy = kSH2a * x; break;
+        case 5: Y = -kSH2a * y * z; gy = -kSH2a * z; gz = -kSH2a * y; break;
+        case 6: Y = kSH2b * (2.f * zz - xx - yy); gx = -2.f * kSH2b * x; gy = -2.f * kSH2b * y; gz = 4.f * kSH2b * z; break;
+        case 7: Y = -kSH2a * x * z; gx = -kSH2a * z; gz = -kSH2a * x; break;
+        case 8: Y = kSH2c * (xx - yy); gx = 2.f * kSH2c * x; gy = -2.f * kSH2c * y; break;
+        case 9: Y = -kSH3a * y * (3.f * xx - yy); gx = -6.f * kSH3a * x * y; gy = -3.f * kSH3a * (xx - yy); break;
+        case 10: Y = kSH3b * x * y * z; gx = kSH3b * y * z; gy = kSH3b * x * z; gz = kSH3b * x * y; break;
+        case 11:
+            Y = -kSH3c * y * (4.f * zz - xx - yy);
+            gx = 2.f * kSH3c * x * y;
+            gy = -kSH3c * (4.f * zz - xx - 3.f * yy);
+            gz = -8.f * kSH3c * y * z;
+            break;
+        case 12:
+            Y = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            gx = -6.f * kSH3d * x * z;
+            gy = -6.f * kSH3d * y * z;
+            gz = kSH3d * (6.f * zz - 3.f * xx - 3.f * yy);
+            break;
+        case 13:
+            Y = -kSH3c * x * (4.f * zz - xx - yy);
+            gx = -kSH3c * (4.f * zz - 3.f * xx - yy);
+            gy = 2.f * kSH3c * x * y;
+            gz = -8.f * kSH3c * x * z;
+            break;
+        case 14: Y = kSH3e * z * (xx - yy); gx = 2.f * kSH3e * x * z; gy = -2.f * kSH3e * y * z; gz = kSH3e * (xx - yy); break;
+        default: Y = -kSH3a * x * (xx - 3.f * yy); gx = -3.f * kSH3a * (xx - yy); gy = 6.f * kSH3a * x * y; break;
+    }
+}
+
 // One Gaussian of preprocess_backward_kernel; shg: its 48 SH coefficients,
 // replaced by their gradients on return.
 __device__ __forceinline__ void preprocess_backward_one(
     const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
     const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
-    const gs_splat *__restrict__ splats, const float *__restrict__ dsplat, float *__restrict__ dmeans,
+    uint32_t tiles, const float *__restrict__ dsplat, float *__restrict__ dmeans,
     float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits) {
-    const uint32_t tiles = reinterpret_cast<const uint32_t *>(splats + gi)[rec::kTiles];
     float *dm = dmeans + 3 * gi;
     float *dls = dlog_scales + 3 * gi;
     float *dq = dquats + 4 * gi;
@@ -445,45 +503,32 @@ __device__ __forceinline__ void preprocess_backward_one(
     const float inv_len = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
     const float x = dx * inv_len, y = dy * inv_len, zz_ = dz * inv_len;
     const float xx = x * x, yy = y * y, zz = zz_ * zz_;
-    float Y[16], Gx[16], Gy[16], Gz[16];
-    Y[0] = kSH0; Gx[0] = Gy[0] = Gz[0] = 0.f;
-    Y[1] = -kSH1 * y; Gx[1] = 0.f; Gy[1] = -kSH1; Gz[1] = 0.f;
-    Y[2] = kSH1 * zz_; Gx[2] = 0.f; Gy[2] = 0.f; Gz[2] = kSH1;
-    Y[3] = -kSH1 * x; Gx[3] = -kSH1; Gy[3] = 0.f; Gz[3] = 0.f;
-    Y[4] = kSH2a * x * y; Gx[4] = kSH2a * y; Gy[4] = kSH2a * x; Gz[4] = 0.f;
-    Y[5] = -kSH2a * y * zz_; Gx[5] = 0.f; Gy[5] = -kSH2a * zz_; Gz[5] = -kSH2a * y;
-    Y[6] = kSH2b * (2.f * zz - xx - yy); Gx[6] = -2.f * kSH2b * x; Gy[6] = -2.f * kSH2b * y; Gz[6] = 4.f * kSH2b * zz_;
-    Y[7] = -kSH2a * x * zz_; Gx[7] = -kSH2a * zz_; Gy[7] = 0.f; Gz[7] = -kSH2a * x;
-    Y[8] = kSH2c * (xx - yy); Gx[8] = 2.f * kSH2c * x; Gy[8] = -2.f * kSH2c * y; Gz[8] = 0.f;
-    Y[9] = -kSH3a * y * (3.f * xx - yy); Gx[9] = -6.f * kSH3a * x * y; Gy[9] = -3.f * kSH3a * (xx - yy); Gz[9] = 0.f;
-    Y[10] = kSH3b * x * y * zz_; Gx[10] = kSH3b * y * zz_; Gy[10] = kSH3b * x * zz_; Gz[10] = kSH3b * x * y;
-    Y[11] = -kSH3c * y * (4.f * zz - xx - yy); Gx[11] = 2.f * kSH3c * x * y;
-    Gy[11] = -kSH3c * (4.f * zz - xx - 3.f * yy); Gz[11] = -8.f * kSH3c * y * zz_;
-    Y[12] = kSH3d * zz_ * (2.f * zz - 3.f * xx - 3.f * yy); Gx[12] = -6.f * kSH3d * x * zz_;
-    Gy[12] = -6.f * kSH3d * y * zz_; Gz[12] = kSH3d * (6.f * zz - 3.f * xx - 3.f * yy);
-    Y[13] = -kSH3c * x * (4.f * zz - xx - yy); Gx[13] = -kSH3c * (4.f * zz - 3.f * xx - yy);
-    Gy[13] = 2.f * kSH3c * x * y; Gz[13] = -8.f * kSH3c * x * zz_;
-    Y[14] = kSH3e * zz_ * (xx - yy); Gx[14] = 2.f * kSH3e * x * zz_; Gy[14] = -2.f * kSH3e * y * zz_;
-    Gz[14] = kSH3e * (xx - yy);
-    Y[15] = -kSH3a * x * (xx - 3.f * yy); Gx[15] = -3.f * kSH3a * (xx - yy); Gy[15] = 6.f * kSH3a * x * y; Gz[15] = 0.f;
     const int ncoef = (sh_degree + 1) * (sh_degree + 1);
     // clamped channels (raw < 0) pass no gradient
-    for (int ch = 0; ch < 3; ++ch) {
-        float raw = 0.5f;
-        for (int k = 0; k < ncoef; ++k) raw = fmaf(shg[3 * k + ch], Y[k], raw);
-        if (raw < 0.f) grgb[ch] = 0.f;
-    }
-    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
     for (int k = 0; k < 16; ++k) {
+        float Yk, gxk, gyk, gzk;
+        sh_term(k, x, y, zz_, xx, yy, zz, Yk, gxk, gyk, gzk);
+        if (k < ncoef)
+            for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(shg[3 * k + ch], Yk, raw[ch]);
+    }
+    for (int ch = 0; ch < 3; ++ch)
+        if (raw[ch] < 0.f) grgb[ch] = 0.f;
+    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        float Yk, gxk, gyk, gzk;
+        sh_term(k, x, y, zz_, xx, yy, zz, Yk, gxk, gyk, gzk);
         const bool on = k < ncoef;
         float gY = 0.f;
         for (int ch = 0; ch < 3; ++ch) {
             gY = fmaf(grgb[ch], on ? shg[3 * k + ch] : 0.f, gY);  // read before the gradient overwrites it
-            dshg[3 * k + ch] = on ? grgb[ch] * Y[k] : 0.f;
+            dshg[3 * k + ch] = on ? grgb[ch] * Yk : 0.f;
         }
-        gdx = fmaf(gY, Gx[k], gdx);
-        gdy = fmaf(gY, Gy[k], gdy);
-        gdz = fmaf(gY, Gz[k], gdz);
+        gdx = fmaf(gY, gxk, gdx);
+        gdy = fmaf(gY, gyk, gdy);
+        gdz = fmaf(gY, gzk, gdz);
     }
     // dir = v / |v|: remove the radial part
     const float radial = gdx * x + gdy * y + gdz * zz_;

@@ -521,6 +521,18 @@ def main():
         b.record(stream)
         torch.cuda.synchronize(dev)
         inv_ms += a.elapsed_time(b) / reps
+    # the contribution-aware (Seele-style) render on the same frames
+    ca_ms = 0.0
+    for k in range(reps):
+        cam = cams[pose_of(k)]
+        r.frame(st, cam)
+        a, b = E(), E()
+        a.record(stream)
+        gs.render_contrib(r.splats, r.vals, r.ranges, cam, (0.0, 0.0, 0.0), r.image, r.final_T, r.n_contrib,
+                          stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ca_ms += a.elapsed_time(b) / reps
 
     # roofline of the dominant kernel (the render: FP32 issue bound)
     peaks = measured_peaks()
@@ -560,6 +572,10 @@ def main():
                              frac=evals_mean * FLOP_PER_EVAL / (inv_ms / 1000.0) / 1e12 / fp32_peak,
                              note="render with the optional inverse-depth output, same poses; work as the "
                                   "render's (the depth channel's FMA not counted)"),
+        render_contrib=dict(ms=ca_ms, tflops=evals_mean * FLOP_PER_EVAL / (ca_ms / 1000.0) / 1e12,
+                            frac=evals_mean * FLOP_PER_EVAL / (ca_ms / 1000.0) / 1e12 / fp32_peak,
+                            note="contribution-aware (Seele-style) render: per-warp vote masks, then the blend of "
+                                 "the masked splats; the same outputs, same poses, work counted as the render's"),
         render=dict(ms=rend_ms, evals=evals_mean, evals_per_s=evals_mean / (rend_ms / 1000.0), tflops=render_tflops,
                     tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
     )

@@ -190,6 +190,16 @@ int gs_sort_status(const void *workspace, int64_t *m_out, void *stream);
 int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
               const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream);
 
+/* gs_render with contribution-aware rasterization, the algorithmic change of
+ * the Seele renderer the paper's case study optimises (Section III): per
+ * staged batch, each group of 32 lanes (one warp, 8x8 pixels) first builds,
+ * by warp votes, the mask of the splats whose alpha reaches 1/255 at one of
+ * the group's still-live pixels, then blends only those; the mask is the
+ * exact per-pixel test, so images, final_T and n_contrib equal gs_render's
+ * bit for bit.  Arguments and errors as gs_render. */
+int gs_render_contrib(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                      const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream);
+
 /* Gradients of a loss with respect to the scene parameters (device, each
  * [n]-major like gs_scene, written -- not accumulated -- by the call). */
 typedef struct gs_scene_grads {

@@ -21,6 +21,7 @@ from .api import (  # noqa: F401
     num_tiles,
     preprocess,
     render,
+    render_contrib,
     render_workload,
     render_invdepth,
     sort,

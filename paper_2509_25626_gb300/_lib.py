@@ -85,6 +85,8 @@ def lib():
         L.gs_sort_static.restype = ctypes.c_int
         L.gs_render_batch.argtypes = [P, P, ctypes.c_int32, P]
         L.gs_render_batch.restype = ctypes.c_int
+        L.gs_render_contrib.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P]
+        L.gs_render_contrib.restype = ctypes.c_int
         L.gs_render_workload.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float), P, P, P, P, P, P]
         L.gs_render_ex.argtypes = [P, P, P, ctypes.POINTER(GsCamera), ctypes.POINTER(c_float)] + [P] * 7
         L.gs_splat_buffer_bytes.argtypes = [ctypes.c_int64]
@@ -140,7 +142,7 @@ def exported_symbols():
     """Names of the gs_* functions the header declares."""
     return ["gs_splat_buffer_bytes", "gs_frame", "gs_preprocess", "gs_camera_block_bytes", "gs_camera_block",
             "gs_preprocess_camblock", "gs_sort_workspace_bytes", "gs_sort", "gs_sort_status", "gs_render",
-            "gs_render_workload", "gs_render_ex", "gs_sort_static", "gs_backward_workspace_bytes",
+            "gs_render_workload", "gs_render_ex", "gs_render_contrib", "gs_sort_static", "gs_backward_workspace_bytes",
             "gs_render_backward", "gs_render_backward_splats", "gs_preprocess_backward",
             "gs_render_batch", "gs_render_balance_workspace_bytes", "gs_render_batch_balanced", "gs_check_wait_timeout",
             "gs_strerror", "gs_last_cuda_error", "gs_version", "gs_built_arch"]

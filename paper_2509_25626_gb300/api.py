@@ -194,6 +194,25 @@ def render(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, 
     return out_color, final_T, n_contrib
 
 
+def render_contrib(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
+                   out_color=None, final_T=None, n_contrib=None, stream=None):
+    """gs_render_contrib: the contribution-aware (Seele-style) render; the
+    same outputs as render(), bit for bit."""
+    dev = splats.device
+    H, W = int(cam.height), int(cam.width)
+    if out_color is None:
+        out_color = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    if final_T is None:
+        final_T = torch.empty((H, W), dtype=torch.float32, device=dev)
+    if n_contrib is None:
+        n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    bgc = (ctypes.c_float * 3)(*[float(v) for v in bg])
+    L.check(L.lib().gs_render_contrib(_ptr(splats), _ptr(vals), _ptr(ranges), ctypes.byref(c), bgc, _ptr(out_color),
+                                      _ptr(final_T), _ptr(n_contrib), _stream(stream)), "gs_render_contrib")
+    return out_color, final_T, n_contrib
+
+
 def render_workload(splats: torch.Tensor, vals: torch.Tensor, ranges: torch.Tensor, cam, bg=(0.0, 0.0, 0.0),
                     stream=None, tile_cycles: bool = False):
     """gs_render_workload: (image, final_T, n_contrib, n_eval [H, W] int32),

@@ -48,6 +48,9 @@ cudaError_t launch_render_batch_balanced(const gs_render_batch_desc *desc, uint3
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,
                           uint32_t *n_eval, uint32_t *tile_cycles, cudaStream_t stream);
+cudaError_t launch_render_contrib(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges,
+                                  const CamParams &cam, const float bg[3], float *out_color, float *final_T,
+                                  uint32_t *n_contrib, cudaStream_t stream);
 
 static_assert(sizeof(gs_splat) == 64 && sizeof(gs_sort_input) == 16, "splat buffer layout");
 
@@ -207,6 +210,23 @@ int gs_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *rang
     gs::NvtxRange nvtx_range("gs_render");
     return render_common(splats, vals, ranges, cam, bg, out_color, final_T, n_contrib, nullptr, nullptr, nullptr,
                          stream);
+}
+
+int gs_render_contrib(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                      const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, void *stream) {
+    gs::NvtxRange nvtx_range("gs_render_contrib");
+    // the argument checks of gs_render (a launch-free call with no outputs
+    // would not be reached: outputs are required)
+    if (!camera_ok(cam) || !bg || !ranges || !aligned(ranges, 8)) return GS_ERR_INVALID_ARG;
+    if (tiles_of(cam) > (uint64_t)INT32_MAX) return GS_ERR_INVALID_ARG;
+    if (!out_color || !final_T || !n_contrib || !aligned(out_color, 4) || !aligned(final_T, 4) ||
+        !aligned(n_contrib, 4))
+        return GS_ERR_INVALID_ARG;
+    if (!splats || !aligned(splats, 16) || !vals || !aligned(vals, 4)) return GS_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(bg[i])) return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_render_contrib(splats, vals, ranges, make_cam_params(*cam), bg, out_color, final_T,
+                                             n_contrib, (cudaStream_t)stream));
 }
 
 int gs_render_workload(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,

@@ -113,7 +113,14 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int width, int height) {
 // job in shared memory, the single-image kernel in its parameters.
 // kBudget: max_rounds is honoured (the split render's budgeted walk); the
 // other walks compile without the round count.
-template <bool kDepth, bool kBudget = false>
+// kContrib: the contribution-aware walk (the Seele-style variant): before
+// blending a round, each warp -- a group of 32 lanes, 8x8 pixels -- builds
+// by warp votes the mask of the splats whose alpha reaches 1/255 at one of
+// its still-live pixels (the exact per-pixel test, on log2 alpha) and then
+// blends only those.  Every other splat would be a no-op for every pixel
+// of the group, so images, n_contrib and the stopping points are those of
+// the plain walk, bit for bit.
+template <bool kDepth, bool kBudget = false, bool kContrib = false>
 __device__ __forceinline__ uint32_t walk_tile(RenderSmem &sm, const gs_render_job &job, uint32_t begin, uint32_t from,
                                               uint32_t to, uint32_t max_rounds, const TileGeom &g, Pixel &p0,
                                               Pixel &p1) {
@@ -162,6 +169,31 @@ __device__ __forceinline__ uint32_t walk_tile(RenderSmem &sm, const gs_render_jo
             cnt += __popc(bal);
         }
         __syncwarp();
+
+        if (kContrib) {
+            // the group's contribution mask, compacted in place (an entry is
+            // written only at or before the one being read)
+            uint32_t kept = 0;
+            for (uint32_t q = 0; q < cnt; ++q) {
+                const uint32_t j = s_list[warp][q];
+                const StagedA sa = s_a[j];
+                const StagedB sb = s_b[j];
+                const float dy = sa.y - pyf;
+                const float dx = sa.x - pxf;
+                const float u0 = fmaf(sa.w00, dx, sa.w01 * dy);
+                const float u1 = u0 - sa.w00;
+                const float v = sb.w11 * dy;
+                const float vv = fmaf(-v, v, sb.lg2o);
+                const bool reach = (!p0.done && fmaf(-u0, u0, vv) >= -kLog2_255) ||
+                                   (!p1.done && fmaf(-u1, u1, vv) >= -kLog2_255);
+                if (__any_sync(0xffffffffu, reach)) {
+                    if (lane == 0) s_list[warp][kept] = (uint8_t)j;
+                    ++kept;
+                }
+            }
+            __syncwarp();
+            cnt = kept;
+        }
 
         const uint32_t pos0 = base - begin + 1;  // list position of staged splat 0
         // the warp votes on stopping once per kVote splats (4 and 64 measured
@@ -236,7 +268,7 @@ __device__ __forceinline__ void store_tile(const gs_render_job &job, const TileG
 // reused for the next tile.  The job's pointers and sizes are read where
 // they are used, not held in registers: the batch kernel keeps its job in
 // shared memory, the single-image kernel in its parameters.
-template <bool kCount, bool kDepth>
+template <bool kCount, bool kDepth, bool kContrib = false>
 __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job &job, const uint2 range, int tile,
                                             float *__restrict__ invdepth, uint32_t *__restrict__ n_eval,
                                             uint32_t *__restrict__ tile_cycles) {
@@ -245,7 +277,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
     const TileGeom g = tile_geom(tile, job.width, job.height);
     Pixel p0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in0};
     Pixel p1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !g.in1};
-    walk_tile<kDepth>(sm, job, range.x, range.x, range.y, 0xffffffffu, g, p0, p1);
+    walk_tile<kDepth, false, kContrib>(sm, job, range.x, range.x, range.y, 0xffffffffu, g, p0, p1);
     store_tile<kCount, kDepth>(job, g, p0, p1, range.y - range.x, invdepth, n_eval);
     if (kCount && tile_cycles != nullptr && threadIdx.x == 0) {
         const long long dt = clock64() - t_start;
@@ -253,7 +285,7 @@ __device__ __forceinline__ void render_tile(RenderSmem &sm, const gs_render_job 
     }
 }
 
-template <bool kCount, bool kDepth>
+template <bool kCount, bool kDepth, bool kContrib = false>
 __global__ void __launch_bounds__(kThreads, (kCount || kDepth) ? 10 : 12) render_kernel(const gs_splat *__restrict__ splats,
                                                           const uint32_t *__restrict__ vals,
                                                           const uint2 *__restrict__ ranges, int width, int height,
@@ -278,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, (kCount || kDepth) ? 10 : 12) render
     job.bg[1] = bg_g;
     job.bg[2] = bg_b;
     job.tile_begin = 0;
-    render_tile<kCount, kDepth>(sm, job, ranges[blockIdx.x], blockIdx.x, invdepth, n_eval, tile_cycles);
+    render_tile<kCount, kDepth, kContrib>(sm, job, ranges[blockIdx.x], blockIdx.x, invdepth, n_eval, tile_cycles);
 }
 
 // --- heavy tiles split across blocks -----------------------------------------
@@ -586,6 +618,16 @@ __global__ void __launch_bounds__(kThreads, 10) split_merge_kernel(const gs_rend
 }
 
 }  // namespace
+
+cudaError_t launch_render_contrib(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges,
+                                  const CamParams &cam, const float bg[3], float *out_color, float *final_T,
+                                  uint32_t *n_contrib, cudaStream_t stream) {
+    const int num_tiles = cam.tiles_x * cam.tiles_y;
+    render_kernel<false, false, true><<<num_tiles, kThreads, 0, stream>>>(
+        splats, vals, reinterpret_cast<const uint2 *>(ranges), cam.width, cam.height, bg[0], bg[1], bg[2], out_color,
+        final_T, n_contrib, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render(const gs_splat *splats, const uint32_t *vals, const uint32_t *ranges, const CamParams &cam,
                           const float bg[3], float *out_color, float *final_T, uint32_t *n_contrib, float *invdepth,

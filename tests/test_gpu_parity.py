@@ -225,6 +225,42 @@ def test_invdepth_parity(case, oracle_frames):
     print(name, "invdepth max err", float(err[exact].max()), "range", float(ref.min()), float(ref.max()))
 
 
+@pytest.mark.parametrize("case", [c[0] for c in SMALL])
+def test_contribution_aware_render_parity(case, oracle_frames):
+    """The contribution-aware (Seele-style) render, gs_render_contrib, on the
+    oracle's records: image, final T and n_contrib equal gs_render's bit for
+    bit (its group masks drop only splats that reach no live pixel of the
+    group), and so meet the parity bar against the oracle."""
+    name, sc, cam = next(c for c in SMALL if c[0] == case)
+    pre, srt, img = oracle_frames[name]
+    rec = to_dev_records(records_from_oracle(pre, SPLAT_DTYPE))
+    vals = torch.from_numpy(np.ascontiguousarray(srt["vals"]).view(np.int32).copy() if srt["m"] else
+                            np.zeros(1, np.int32)).to(DEV)
+    ranges = torch.from_numpy(srt["ranges"].view(np.int32).copy()).to(DEV)
+    bg = (0.1, 0.2, 0.3)
+    out_c, T_c, nc_c = gs.render_contrib(rec, vals, ranges, cam, bg)
+    out, T, nc = gs.render(rec, vals, ranges, cam, bg=bg)
+    torch.cuda.synchronize()
+    assert torch.equal(out_c, out) and torch.equal(T_c, T) and torch.equal(nc_c, nc)
+    compare_images(out_c.cpu().numpy(), T_c.cpu().numpy(), nc_c.cpu().numpy(), img)
+
+
+def test_contribution_aware_render_full_size():
+    """At the benchmark's size (3M Gaussians, 1600x1064, two orbit poses):
+    gs_render_contrib equals gs_render bit for bit."""
+    sc = clustered_scene(3_000_000, seed=1)
+    st = SceneTensors.from_scene(sc, DEV)
+    for k in (0, 9):
+        cam = orbit_camera(k, 20, 4.0, 1600, 1064)
+        r = gs.Renderer(sc.n, cam.width, cam.height, 16_000_000)
+        r.frame(st, cam)
+        ref = [t.clone() for t in (r.image, r.final_T, r.n_contrib)]
+        out = gs.render_contrib(r.splats, r.vals, r.ranges, cam)
+        torch.cuda.synchronize()
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b)
+
+
 def test_batches_stop_permanently(oracle):
     """A tile with 600 stacked splats that saturates in the first batch of
     256: the pixel must not resume in later batches (a failure mode the

@@ -68,6 +68,25 @@ def parse_args():
     return p.parse_args()
 
 
+def scene_recipe(workload: str) -> dict:
+    """The generator settings of the workload's synthetic scene, as the
+    bench line states them (the defaults of synth.clustered_scene for the
+    clustered workloads)."""
+    import inspect
+    from synth import clustered_scene
+    if workload == "fwd_16k_256":
+        return dict(generator="uniform_box_scene", seed=0)
+    p = {k: v.default for k, v in inspect.signature(clustered_scene).parameters.items()
+         if v.default is not inspect.Parameter.empty}
+    seeds = {"fwd_3m_1600x1064": 1, "bwd_1m_1237x822": 3, "slab_6m_3840x2160x8": 5}
+    return dict(generator="clustered_scene", seed=seeds.get(workload), n_clusters=p["n_clusters"],
+                shell_frac=p["shell_frac"], shell_r=list(p["shell_r"]), ball_r=p["ball_r"],
+                axis_std=list(p["axis_std"]), log_scale="centre + t_scale * Student-t(3), clipped",
+                log_scale_centre=p["log_scale_centre"], log_scale_t_scale=p["log_scale_t_scale"],
+                log_scale_clip=list(p["log_scale_clip"]), opacity_logit_std=p["opacity_std"],
+                sh="DC N(0, 0.5), higher bands N(0, 0.05)")
+
+
 def rank_pose(k: int, world: int, rank: int, n_poses: int) -> int:
     """Pose rendered by `rank` at step k: ranks interleave over the orbit, so
     the N replicas render disjoint poses each step (weak scaling, no data
@@ -235,7 +254,7 @@ def run_reference(args):
         warmup=args.warmup, ms_per_step=1000.0 * statistics.mean(times), higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
         config=dict(workload=args.workload, gaussians=scene.n, width=cams[0].width, height=cams[0].height,
-                    poses=len(cams)),
+                    poses=len(cams), scene_recipe=scene_recipe(args.workload)),
         cpu_baseline=dict(value=fps, unit="frames/s", cores=cores, kind="oracle",
                           sample="per step: FP64 oracle preprocess + duplicate/sort of a whole frame and one "
                                  "16-pixel tile row of its render, extrapolated to the full frame"),
@@ -642,7 +661,7 @@ def main():
             config=dict(workload=args.workload, gaussians=n, width=W, height=H, poses=P, tiles=T,
                         instances_mean=ms_mean, visible_pose0=vis[0], evals_mean=evals_mean,
                         m_cap=m_cap, parallelism=f"replicas{world}", frames_in_flight=F,
-                        serial_frames_per_s=serial_fps,
+                        serial_frames_per_s=serial_fps, scene_recipe=scene_recipe(args.workload),
                         l2="inputs larger than L2: the 708 MB scene is re-read from HBM every frame"),
             roofline=roofline, frame_roofline=frame_roofline, kernels=kernels, cpu_baseline=cpu, e2e=e2e,
             e2e_resident_scene=e2e_resident,

@@ -341,6 +341,28 @@ def test_sort_wide_and_tall_images(oracle, wh):
     assert np.array_equal(ranges, srt["ranges"])
 
 
+@pytest.mark.parametrize("wh,ls", [((4096, 40), (-5.0, 0.6)), ((40, 4096), (-5.0, 0.6)), ((320, 16), (-3.0, 0.9)),
+                                   ((16, 320), (-3.0, 0.9)), ((1024, 1024), (-0.5, 1.2))])
+def test_sort_grid_edges(oracle, wh, ls):
+    """Tile grids at the edges of the one-byte tile coordinates: exactly 256
+    tiles wide or tall, a single tile row or column, and splats so large that
+    one splat duplicates into a thousand instances or more (2M instances from
+    600 Gaussians).  Keys, values and ranges bit-exact on the oracle's
+    records."""
+    w, h = wh
+    sc, cam = tiny_scene(600 if ls[0] > -1.0 else 4000, w + 3 * h, w, h, log_scale=ls)
+    pre = oracle.preprocess(sc, cam)
+    srt = oracle.duplicate_sort(pre, cam)
+    rec = records_from_oracle(pre, SPLAT_DTYPE)
+    keys, vals, ranges, m, _, _ = gpu_sort(to_dev_records(rec), sc.n, cam, max(int(srt["m"]), 1))
+    assert m == srt["m"] and m > 0
+    if ls[0] > -1.0:
+        assert m > 1_000_000
+    assert np.array_equal(keys, srt["keys"])
+    assert np.array_equal(vals, srt["vals"])
+    assert np.array_equal(ranges, srt["ranges"])
+
+
 def test_capacity_overflow_reported():
     sc, cam = tiny_scene(2000, 4, 128, 96, log_scale=(-2.8, 0.6))
     st = SceneTensors.from_scene(sc, DEV)

@@ -270,15 +270,7 @@ class Server:
             t = now()
             # admission: arrived requests while a slot of their scene is free;
             # with work in flight, only once overlap_min of them are waiting
-            if (rendering or prepared) and realtime and self.overlap_min > 1:
-                arrived = 0
-                for r in pending:
-                    if r.arrival > t or arrived >= self.overlap_min:
-                        break
-                    arrived += 1
-                admit = arrived >= self.overlap_min
-            else:
-                admit = True
+            admit = may_admit(pending, t, bool(rendering or prepared), realtime, self.overlap_min)
             while admit and pending and (not realtime or pending[0].arrival <= t):
                 req = pending[0]
                 if not free[req.scene]:
@@ -300,12 +292,8 @@ class Server:
             # engine is free: the render stream waits for their sorts on the
             # device, so no host round trip sits between a sort and its render
             if rendering is None and prepared:
-                take = min(len(prepared), self.max_batch)
-                if self.ready_only and len(prepared) <= self.ready_only_max:
-                    ready = 1  # the oldest, even if its sort is still running
-                    while ready < take and prepared[ready][2].query():
-                        ready += 1
-                    take = ready
+                take = batch_size([ev for _, _, ev in prepared], self.max_batch,
+                                  self.ready_only_max if self.ready_only else 0)
                 batch, prepared = prepared[:take], prepared[take:]
                 jobs = []
                 for req, slot, _ in batch:
@@ -369,6 +357,35 @@ class Server:
             slot.stream.synchronize()
             self._finish(req, slot, now(), done)
         return done, now()
+
+
+def may_admit(pending, t: float, in_flight: bool, realtime: bool, overlap_min: int) -> bool:
+    """The admission rule of Server.serve: with nothing in flight (or in a
+    saturation run) arrived requests are admitted at once; with a request in
+    flight, only once at least overlap_min of them have arrived.  pending:
+    the requests not yet admitted, by arrival time."""
+    if not in_flight or not realtime or overlap_min <= 1:
+        return True
+    arrived = 0
+    for r in pending:
+        if r.arrival > t or arrived >= overlap_min:
+            break
+        arrived += 1
+    return arrived >= overlap_min
+
+
+def batch_size(events, max_batch: int, ready_only_max: int) -> int:
+    """How many prepared requests (in admission order; events: their sorts'
+    completion events, each with .query()) the next batch takes: up to
+    max_batch, and, while at most ready_only_max are prepared, only the
+    leading ones whose sort has finished -- the oldest always."""
+    take = min(len(events), max_batch)
+    if 0 < len(events) <= ready_only_max:
+        ready = 1
+        while ready < take and events[ready].query():
+            ready += 1
+        take = ready
+    return take
 
 
 def poisson_requests(rate: float, duration: float, scenes: list[str], resolutions: list[tuple], cam_fn, seed: int = 0):

@@ -244,17 +244,42 @@ constexpr float kSH3e = 1.445305721320277f;
 constexpr int kPreBackThreads = 128;
 constexpr int kShStride = 49;  // 48 floats + 1: rows start in different banks
 
-__device__ __forceinline__ void preprocess_backward_one(
-    const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
-    const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
-    uint32_t tiles, const float *__restrict__ dsplat, float *__restrict__ dmeans,
-    float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits);
+// A visible Gaussian's inputs to the backward, loaded before its SH
+// coefficients are staged so that both sets of loads are in flight at once.
+struct GaussIn {
+    float G[9];  // dL/d(x, y, conic a, b, c, opacity, r, g, b)
+    float m[3], ls[3], logit;
+    float4 q;
+};
 
-#ifdef GS_PREBACK_MIN_BLOCKS
-#define GS_PREBACK_BOUNDS __launch_bounds__(kPreBackThreads, GS_PREBACK_MIN_BLOCKS)
-#else
-#define GS_PREBACK_BOUNDS __launch_bounds__(kPreBackThreads)
+__device__ __forceinline__ GaussIn load_gauss_in(const float *__restrict__ means, const float *__restrict__ log_scales,
+                                                 const float4 *__restrict__ quats, const float *__restrict__ logits,
+                                                 const float *__restrict__ dsplat, int64_t gi) {
+    GaussIn in;
+    const float *G = dsplat + 12 * gi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) in.G[k] = G[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        in.m[k] = means[3 * gi + k];
+        in.ls[k] = log_scales[3 * gi + k];
+    }
+    in.q = quats[gi];
+    in.logit = logits[gi];
+    return in;
+}
+
+__device__ __forceinline__ void preprocess_backward_one(const GaussIn &in, float *shg, int64_t gi, int sh_degree,
+                                                        const CamParams &cam, uint32_t tiles,
+                                                        float *__restrict__ dmeans, float *__restrict__ dlog_scales,
+                                                        float *__restrict__ dquats, float *__restrict__ dlogits);
+
+// 6 blocks per SM (80 registers): with the inputs held across the SH
+// staging the kernel would take 92 registers and 5 blocks, measured slower.
+#ifndef GS_PREBACK_MIN_BLOCKS
+#define GS_PREBACK_MIN_BLOCKS 6
 #endif
+#define GS_PREBACK_BOUNDS __launch_bounds__(kPreBackThreads, GS_PREBACK_MIN_BLOCKS)
 __global__ void GS_PREBACK_BOUNDS preprocess_backward_kernel(
     const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
     const float *__restrict__ logits, const float *__restrict__ sh, int64_t n, int sh_degree, CamParams cam,
@@ -274,6 +299,9 @@ __global__ void GS_PREBACK_BOUNDS preprocess_backward_kernel(
     const uint4 *sort_in = reinterpret_cast<const uint4 *>(splats + n);
     if ((int)threadIdx.x < nb) s_tiles[threadIdx.x] = __ldg(&sort_in[g0 + threadIdx.x].y);
     __syncthreads();
+    const int64_t gi = g0 + threadIdx.x;
+    GaussIn in{};
+    if (gi < n && s_tiles[threadIdx.x]) in = load_gauss_in(means, log_scales, quats, logits, dsplat, gi);
     // full blocks with 16-byte aligned SH arrays move them as float4, all 12
     // loads of a thread in flight at once
     const bool vec = nb == kPreBackThreads &&
@@ -299,9 +327,9 @@ __global__ void GS_PREBACK_BOUNDS preprocess_backward_kernel(
             s_sh[f / 48][f % 48] = s_tiles[f / 48] ? sh[g0 * 48 + f] : 0.f;
     }
     __syncthreads();
-    const int64_t gi = g0 + threadIdx.x;
-    if (gi < n) preprocess_backward_one(means, log_scales, quats, logits, s_sh[threadIdx.x], gi, sh_degree, cam,
-                                        s_tiles[threadIdx.x], dsplat, dmeans, dlog_scales, dquats, dlogits);
+    if (gi < n)
+        preprocess_backward_one(in, s_sh[threadIdx.x], gi, sh_degree, cam, s_tiles[threadIdx.x], dmeans, dlog_scales,
+                                dquats, dlogits);
     __syncthreads();
     if (vec) {
         float4 *dst = reinterpret_cast<float4 *>(dsh + g0 * 48);
@@ -360,11 +388,10 @@ __device__ __forceinline__ void sh_term(int k, float x, float y, float z, float 
 
 // One Gaussian of preprocess_backward_kernel; shg: its 48 SH coefficients,
 // replaced by their gradients on return.
-__device__ __forceinline__ void preprocess_backward_one(
-    const float *__restrict__ means, const float *__restrict__ log_scales, const float4 *__restrict__ quats,
-    const float *__restrict__ logits, float *shg, int64_t gi, int sh_degree, const CamParams &cam,
-    uint32_t tiles, const float *__restrict__ dsplat, float *__restrict__ dmeans,
-    float *__restrict__ dlog_scales, float *__restrict__ dquats, float *__restrict__ dlogits) {
+__device__ __forceinline__ void preprocess_backward_one(const GaussIn &in, float *shg, int64_t gi, int sh_degree,
+                                                        const CamParams &cam, uint32_t tiles,
+                                                        float *__restrict__ dmeans, float *__restrict__ dlog_scales,
+                                                        float *__restrict__ dquats, float *__restrict__ dlogits) {
     float *dm = dmeans + 3 * gi;
     float *dls = dlog_scales + 3 * gi;
     float *dq = dquats + 4 * gi;
@@ -376,20 +403,20 @@ __device__ __forceinline__ void preprocess_backward_one(
         for (int k = 0; k < 48; ++k) dshg[k] = 0.f;
         return;
     }
-    const float *G = dsplat + 12 * gi;
+    const float *G = in.G;
     const float gx = G[0], gy = G[1], ga = G[2], gb = G[3], gc = G[4], gop = G[5];
     float grgb[3] = {G[6], G[7], G[8]};
-    const float mx = means[3 * gi], my = means[3 * gi + 1], mz = means[3 * gi + 2];
+    const float mx = in.m[0], my = in.m[1], mz = in.m[2];
     const float *V = cam.V;
     const float z = fmaf(V[10], mz, fmaf(V[9], my, fmaf(V[8], mx, V[11])));
     const float tx = fmaf(V[2], mz, fmaf(V[1], my, fmaf(V[0], mx, V[3])));
     const float ty = fmaf(V[6], mz, fmaf(V[5], my, fmaf(V[4], mx, V[7])));
 
     // forward recomputation
-    const float4 q4 = quats[gi];
+    const float4 q4 = in.q;
     const float qinv = 1.0f / sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
-    const float s[3] = {expf(log_scales[3 * gi]), expf(log_scales[3 * gi + 1]), expf(log_scales[3 * gi + 2])};
+    const float s[3] = {expf(in.ls[0]), expf(in.ls[1]), expf(in.ls[2])};
     const float R[3][3] = {
         {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
         {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
@@ -538,7 +565,7 @@ __device__ __forceinline__ void preprocess_backward_one(
     for (int c = 0; c < 3; ++c) dm[c] = gm[c];
 
     // opacity = sigmoid(logit)
-    const float o = 1.0f / (1.0f + expf(-logits[gi]));
+    const float o = 1.0f / (1.0f + expf(-in.logit));
     dlogits[gi] = gop * o * (1.0f - o);
 }
 

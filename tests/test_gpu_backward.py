@@ -80,6 +80,31 @@ def test_backward_matches_oracle_gradient(oracle, case):
     print(name, {k: f"{v:.2e}" for k, v in report.items()})
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_backward_lower_sh_degrees(oracle, deg):
+    """SH degrees 0-2: the colour uses (deg + 1)^2 coefficients, the
+    gradients of the others are exactly zero, and every tensor matches the
+    oracle's FP64 gradient at the same bar as degree 3."""
+    from oracle import grad as G
+    from parity import POS_EPS_E2E, TAU_ALPHA, TAU_T
+    from synth import Scene
+    base, cam = grad_scene(seed=3)
+    sc = Scene(*base.arrays(), sh_degree=deg)
+    dL = np.random.default_rng(2).normal(size=(3, cam.height, cam.width))
+    pre, srt, ora = oracle.frame(sc, cam, BG, TAU_ALPHA, TAU_T, pos_eps=POS_EPS_E2E)
+    dL[:, ora["near"] > 0] = 0.0
+    g_gpu, (img, T, nc), recs = gpu_grads(sc, cam, dL, forward=True)
+    assert no_rect_flips(recs, pre)
+    exact = ora["near"] == 0
+    assert np.array_equal(nc[exact], ora["n_contrib"][exact])
+    _, _, g_ref = G.forward_and_grad(sc, cam, dL, BG)
+    ncoef = (deg + 1) ** 2
+    assert not np.any(g_gpu["sh"][:, ncoef:, :]), "bands above the degree get zero gradient"
+    assert np.any(g_gpu["sh"][:, :ncoef, :])
+    for k in NAMES:
+        assert rel_err(g_gpu[k], g_ref[k]) <= 1e-3, (deg, k, rel_err(g_gpu[k], g_ref[k]))
+
+
 @pytest.mark.parametrize("scene", ["grad5", "clamp6"])
 def test_backward_matches_central_differences(oracle, scene):
     """Direct check against FP64 central differences of the C oracle, also

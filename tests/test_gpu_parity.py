@@ -106,6 +106,39 @@ def test_splat_buffer_sort_inputs_repeat_the_records():
     assert np.array_equal(tail, recs[:, 12:16])
 
 
+def test_preprocess_from_camera_block_equals_preprocess():
+    """gs_preprocess_camblock (the camera read from a device camera block, as
+    the server's captured graphs do) writes the same splat buffer as
+    gs_preprocess, bit for bit, for several poses and image sizes."""
+    import ctypes
+    from paper_2509_25626_gb300 import _lib as L
+    from paper_2509_25626_gb300.api import _ptr, camera_struct, splat_buffer
+    sc = clustered_scene(30000, seed=4)
+    st = SceneTensors.from_scene(sc, DEV)
+    nbytes = L.lib().gs_camera_block_bytes()
+    for k, (w, h) in ((0, (320, 240)), (5, (97, 61)), (11, (640, 480))):
+        cam = orbit_camera(k, 20, 4.0, w, h)
+        ref = gs.preprocess(st, cam)
+        host = torch.zeros(128, dtype=torch.uint8)
+        assert L.lib().gs_camera_block(ctypes.byref(camera_struct(cam)), ctypes.c_void_p(host.data_ptr())) == 0
+        block = host[:nbytes].to(DEV)
+        out = splat_buffer(sc.n, torch.device(DEV))
+        stream = torch.cuda.current_stream()
+        assert L.lib().gs_preprocess_camblock(ctypes.byref(st.struct()), _ptr(block), _ptr(out),
+                                              ctypes.c_void_p(int(stream.cuda_stream))) == 0
+        torch.cuda.synchronize()
+        # every record's last 32 bytes and the dense sort inputs; the first 32
+        # bytes of a visible one (a culled one's are left unwritten)
+        n = sc.n
+        a = out.view(torch.int32).reshape(-1)[: 20 * n].cpu().numpy()
+        b = ref.view(torch.int32).reshape(-1)[: 20 * n].cpu().numpy()
+        ra, rb = a[: 16 * n].reshape(n, 16), b[: 16 * n].reshape(n, 16)
+        vis = rb[:, 13] > 0  # tiles_touched
+        assert vis.any() and not vis.all()
+        assert np.array_equal(ra[:, 8:], rb[:, 8:]) and np.array_equal(a[16 * n:], b[16 * n:]), (k, w, h)
+        assert np.array_equal(ra[vis, :8], rb[vis, :8]), (k, w, h)
+
+
 @pytest.mark.parametrize("case", [c[0] for c in SMALL])
 def test_sort_bit_exact_on_oracle_records(case, oracle_frames):
     """gs_sort on the oracle's own preprocess output: keys, values and

@@ -381,7 +381,7 @@ def main():
 
     # evaluations per pose (untimed), the render's work count, and the
     # per-tile block cycles (load balance)
-    evals, tile_stats, vis, front = [], [], [], []
+    evals, tile_stats, vis, front, work_stats = [], [], [], [], []
     for cam in cams:
         gs.preprocess(st, cam, r.splats)
         words = r.splats.view(torch.int32)[:n]
@@ -391,6 +391,7 @@ def main():
         _, _, _, ne, cyc = gs.render_workload(r.splats, r.vals, r.ranges, cam, tile_cycles=True)
         evals.append(int(ne.to(torch.int64).sum().item()))
         tile_stats.append(tile_cycle_stats(cyc))
+        work_stats.append(tile_workload_stats(r.ranges, ne, W, H))
 
     stream = torch.cuda.current_stream(dev)
     pose_of = lambda k: rank_pose(k, world, rank, P)
@@ -596,7 +597,8 @@ def main():
                             note="contribution-aware (Seele-style) render: per-warp vote masks, then the blend of "
                                  "the masked splats; the same outputs, same poses, work counted as the render's"),
         render=dict(ms=rend_ms, evals=evals_mean, evals_per_s=evals_mean / (rend_ms / 1000.0), tflops=render_tflops,
-                    tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]}),
+                    tile_cycles={k: statistics.mean(t[k] for t in tile_stats) for k in tile_stats[0]},
+                    workload={k: statistics.mean(t[k] for t in work_stats) for k in work_stats[0]}),
     )
     # kernels per frame: preprocess; compact, 4 depth radix passes, offsets,
     # duplicate fused with the first tile pass, one more pass per further
@@ -674,6 +676,24 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def tile_workload_stats(ranges, n_eval, width: int, height: int) -> dict:
+    """The per-tile and per-thread workload the paper characterises (Table
+    III): Gaussians per tile (list length) over every tile, mean and
+    variance; and, per pixel of a non-empty tile, the fraction of its tile's
+    list it evaluates before stopping, mean and variance."""
+    import torch
+    r = ranges.to(torch.int64)
+    lens = (r[:, 1] - r[:, 0]).to(torch.float64)
+    tiles_x = (width + 15) // 16
+    py = torch.arange(height, device=lens.device).view(-1, 1) // 16
+    px = torch.arange(width, device=lens.device).view(1, -1) // 16
+    per_px = lens[(py * tiles_x + px).reshape(-1)].reshape(height, width)
+    ok = per_px > 0
+    frac = n_eval.to(torch.float64)[ok] / per_px[ok]
+    return dict(gaussians_per_tile_mean=float(lens.mean()), gaussians_per_tile_var=float(lens.var(unbiased=False)),
+                evaluated_fraction_mean=float(frac.mean()), evaluated_fraction_var=float(frac.var(unbiased=False)))
 
 
 def tile_cycle_stats(cyc) -> dict:

@@ -158,14 +158,15 @@ def clustered_scene(n: int = 3_000_000, seed: int = 1, n_clusters: int = 64,
                     shell_frac: float = 0.2, shell_r: tuple = (10.0, 50.0),
                     ball_r: float = 3.0, axis_std: tuple = (0.05, 0.8),
                     log_scale_centre: float = -5.0, log_scale_t_scale: float = 0.25,
-                    log_scale_clip: tuple = (-12.0, -2.0), opacity_std: float = 1.5) -> Scene:
+                    log_scale_clip: tuple = (-12.0, -2.0), opacity_std: float = 1.5,
+                    opacity_centre: float = 0.0) -> Scene:
     """Mixture of ``n_clusters`` anisotropic Gaussian clusters (centres uniform
     in a ball of radius ``ball_r``, random orientation, axis standard
     deviations log-uniform in ``axis_std``) plus a ``shell_frac`` share of
     points uniform in direction at radius U[shell_r].  Log-scales are
     ``log_scale_centre`` + ``log_scale_t_scale`` * Student-t(3) per axis,
-    clipped to ``log_scale_clip``; opacity logits N(0, ``opacity_std``); SH as
-    in ``uniform_box_scene``.
+    clipped to ``log_scale_clip``; opacity logits N(``opacity_centre``,
+    ``opacity_std``); SH as in ``uniform_box_scene``.
 
     With the defaults, at 3M points and 1600x1064 on the orbit poses, each
     16x16 tile overlaps about 1.4e3 Gaussians on average with variance/mean^2
@@ -193,7 +194,7 @@ def clustered_scene(n: int = 3_000_000, seed: int = 1, n_clusters: int = 64,
     log_scales = np.clip(log_scale_centre + log_scale_t_scale * rng.standard_t(3, size=(n, 3)),
                          *log_scale_clip)
     quats = _unit_quats(rng, n)
-    logits = rng.normal(0.0, opacity_std, size=n)
+    logits = rng.normal(opacity_centre, opacity_std, size=n)
     return Scene(_f32(means), _f32(log_scales), quats, _f32(logits), _sh(rng, n))
 
 
@@ -233,7 +234,7 @@ def tiny_scene(n: int, seed: int, width: int, height: int, fov_x_deg: float = 60
     means = np.stack([x, y, z], axis=1)
     log_scales = rng.normal(log_scale[0], log_scale[1], size=(n, 3))
     quats = _unit_quats(rng, n)
-    logits = rng.normal(0.0, opacity_std, size=n)
+    logits = rng.normal(opacity_centre, opacity_std, size=n)
     return Scene(_f32(means), _f32(log_scales), quats, _f32(logits), _sh(rng, n)), cam
 
 

@@ -234,7 +234,7 @@ def tiny_scene(n: int, seed: int, width: int, height: int, fov_x_deg: float = 60
     means = np.stack([x, y, z], axis=1)
     log_scales = rng.normal(log_scale[0], log_scale[1], size=(n, 3))
     quats = _unit_quats(rng, n)
-    logits = rng.normal(opacity_centre, opacity_std, size=n)
+    logits = rng.normal(0.0, opacity_std, size=n)
     return Scene(_f32(means), _f32(log_scales), quats, _f32(logits), _sh(rng, n)), cam
 
 

@@ -374,7 +374,9 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
     const unsigned lt = lanemask_lt();
     const uint32_t wbase = start + warp * (IPT * 32) + lane;
     // stable warp-local ranking (sm.wcnt is zero on entry)
-    uint32_t rank[IPT];
+    uint32_t rank2[(IPT + 1) / 2];  // ranks (< 2^16: a warp ranks <= 32 IPT elements), two per register
+#pragma unroll
+    for (int k = 0; k < (IPT + 1) / 2; ++k) rank2[k] = 0u;
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
         const bool valid = wbase + k * 32 < n;
@@ -385,7 +387,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
         __syncwarp();
         if (valid && (peers & lt) == 0) sm.wcnt[warp][d] = old + (uint32_t)__popc(peers);
         __syncwarp();
-        rank[k] = old + (uint32_t)__popc(peers & lt);
+        rank2[k / 2] |= (old + (uint32_t)__popc(peers & lt)) << (16 * (k & 1));
     }
     __syncthreads();
     // digit t: prefix over warps, this block's count, and its start in the block
@@ -419,7 +421,7 @@ __device__ __forceinline__ void rank_scatter(SweepSmemT<NT, ITEMS> &sm, const ui
     for (int k = 0; k < IPT; ++k) {
         if (wbase + k * 32 < n) {
             const uint32_t d = (key[k] >> shift) & 0xffu;
-            const uint32_t pos = sm.wcnt[warp][d] + rank[k];
+            const uint32_t pos = sm.wcnt[warp][d] + ((rank2[k / 2] >> (16 * (k & 1))) & 0xffffu);
             sm.keys[pos] = key[k];
             sm.vals[pos] = vals[k];
         }

@@ -972,6 +972,8 @@ def measure_backward(gs, dev, steps: int, warmup: int):
     g = torch.Generator(device=dev).manual_seed(0)
     dL = torch.randn((3, cams[0].height, cams[0].width), generator=g, device=dev)
     def step(k):
+        for p_ in params:  # as zero_grad(set_to_none=True): the new gradients are assigned, not added
+            p_.grad = None
         img = gs.rasterize(*params, cams[k % len(cams)], (0.0, 0.0, 0.0), 3)
         img.backward(dL)
     for k in range(warmup):
@@ -1033,7 +1035,8 @@ def measure_backward(gs, dev, steps: int, warmup: int):
                                  bound="hbm"))
     return dict(workload="bwd_1m_1237x822", gaussians=scene.n, width=cams[0].width, height=cams[0].height,
                 steps=steps, ms_per_step=ms, steps_per_s=1000.0 / ms, kernels=kernels,
-                note="forward + backward through gs.rasterize (one host sync per forward for the sort's M)")
+                note="forward + backward through gs.rasterize (one host sync per forward for the sort's M); "
+                     "parameter gradients set to None before each step, as zero_grad does")
 
 
 def kernel_sha(*names: str) -> str:
